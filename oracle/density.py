@@ -1,0 +1,174 @@
+"""Oracle: nodal density, band energy, adjoint and forces.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+For node j with region R(j) and poles (z_p, w_p):
+
+* density (Eq. Electron_density:GQ with g -> r):
+      rho_j = (2/dV) sum_p Im( w_p x_jp(j) ),  (H_R - z_p) x_jp = e_j
+* band energy per node (first term of Eq. tot, 2 [H r(H)]_jj, using
+  eps r(eps) = sum_p Im(w_p + w_p z_p/(eps - z_p))):
+      e_j = 2 sum_p Im( w_p (1 + z_p x_jp(j)) )
+* adjoint: with G = (H_R - z)^-1 complex symmetric, dG_jj/dV_k = -G_jk^2 =
+  -x_jp(k)^2, so for L(rho, e) with a_j = dL/drho_j, b_j = dL/de_j:
+      dL/dV_k = -sum_j sum_p Im( (2 a_j/dV + 2 b_j z_p) w_p x_jp(k)^2 )
+* Hellmann-Feynman forces (Section 2.1, last paragraph) through the local
+  potential only:  F_a = -sum_k dL/dV_k dV_k/dR_a.
+
+The Python side gathers each region and its projectors; the C side
+(``cocg.c``) runs COCG per system.
+"""
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import hamiltonian as ham_mod
+from . import poles as poles_mod
+from ._native import load_cocg
+
+
+@dataclass
+class OracleHamiltonian:
+    V: np.ndarray
+    projs: list
+    stencil: ham_mod.Stencil
+    emin: float
+    emax: float
+
+
+def build(w) -> OracleHamiltonian:
+    V = ham_mod.local_potential(w)
+    projs = ham_mod.projectors(w)
+    st = ham_mod.kinetic_stencil(w.spacing, w.fd_order)
+    emin, emax = ham_mod.gershgorin_bounds(w, V, projs)
+    return OracleHamiltonian(V=V, projs=projs, stencil=st, emin=emin, emax=emax)
+
+
+def poles_for(w, H: OracleHamiltonian):
+    return poles_mod.fermi_poles(w.kT, w.mu, H.emin, H.emax, w.n_poles)
+
+
+@dataclass
+class OracleResult:
+    rho: np.ndarray        # (n_nodes,)
+    e_node: np.ndarray     # (n_nodes,)
+    x_src: np.ndarray      # (n_nodes, P) complex
+    iters: np.ndarray      # (n_nodes, P)
+    resid: np.ndarray      # (n_nodes, P)
+    status: np.ndarray     # (n_nodes, P)
+    z: np.ndarray
+    wts: np.ndarray
+    regions: list
+    x_full: list           # per node: (P, n_region) complex, or None
+
+
+def _pack(w, H, nodes, halfwidth):
+    regions = [ham_mod.region_of(w, int(n), int(s)) for n, s in zip(nodes, halfwidth)]
+    dims = np.array([r.dims for r in regions], dtype=np.int32).reshape(-1)
+    ring = np.array([r.ring for r in regions], dtype=np.int32).reshape(-1)
+    src = np.array([r.src for r in regions], dtype=np.int32)
+    sizes = np.array([len(r.gidx) for r in regions], dtype=np.int64)
+    voff = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    Vp = np.concatenate([H.V[r.gidx] for r in regions]).astype(np.float64)
+    pptr_reg = [0]
+    p_ptr = [0]
+    p_idx, p_val, p_E = [], [], []
+    for r in regions:
+        plist = ham_mod.projectors_in_region(H.projs, r, w.n_grid)
+        for li, val, e in plist:
+            p_idx.append(li.astype(np.int32))
+            p_val.append(val.astype(np.float64))
+            p_E.append(e)
+            p_ptr.append(p_ptr[-1] + len(li))
+        pptr_reg.append(pptr_reg[-1] + len(plist))
+    p_idx = np.concatenate(p_idx) if p_idx else np.zeros(1, np.int32)
+    p_val = np.concatenate(p_val) if p_val else np.zeros(1, np.float64)
+    p_E = np.array(p_E if p_E else [0.0], dtype=np.float64)
+    return (regions, dims, ring, src, voff, Vp, np.array(pptr_reg, np.int64),
+            np.array(p_ptr, np.int64), p_idx, p_val, p_E, sizes)
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def solve(w, H: OracleHamiltonian = None, z=None, wts=None, tol: float = 1e-12,
+          maxit: int = None, keep_x: bool = False) -> OracleResult:
+    """Run every (node, pole) system of the workload."""
+    if H is None:
+        H = build(w)
+    if z is None:
+        z, wts = poles_for(w, H)
+    maxit = int(maxit if maxit is not None else w.maxit)
+    (regions, dims, ring, src, voff, Vp, pptr_reg, p_ptr, p_idx, p_val, p_E,
+     sizes) = _pack(w, H, w.nodes, w.halfwidth)
+    n_nodes, P = len(regions), len(z)
+    n_sys = n_nodes * P
+    sys_reg = np.repeat(np.arange(n_nodes, dtype=np.int32), P)
+    sys_z = np.empty(2 * n_sys)
+    zz = np.tile(z, n_nodes)
+    sys_z[0::2], sys_z[1::2] = zz.real, zz.imag
+    x_src = np.zeros(2 * n_sys)
+    iters = np.zeros(n_sys, np.int32)
+    resid = np.zeros(n_sys)
+    status = np.zeros(n_sys, np.int32)
+    if keep_x:
+        sys_sizes = np.repeat(sizes, P)
+        sys_xoff = np.concatenate([[0], np.cumsum(sys_sizes)[:-1]]).astype(np.int64)
+        x_full = np.zeros(2 * int(sys_sizes.sum()))
+        xf_ptr, xo_ptr = _ptr(x_full, ctypes.c_double), _ptr(sys_xoff, ctypes.c_longlong)
+    else:
+        x_full, sys_xoff = None, None
+        xf_ptr, xo_ptr = None, None
+    st = H.stencil
+    coef = np.ascontiguousarray(st.coef.reshape(-1))
+    lib = load_cocg()
+    lib.oracle_cocg_batch(
+        n_sys, _ptr(sys_reg, ctypes.c_int), _ptr(sys_z, ctypes.c_double),
+        _ptr(dims, ctypes.c_int), _ptr(ring, ctypes.c_int), _ptr(src, ctypes.c_int),
+        _ptr(voff, ctypes.c_longlong), _ptr(Vp, ctypes.c_double),
+        _ptr(pptr_reg, ctypes.c_longlong), _ptr(p_ptr, ctypes.c_longlong),
+        _ptr(p_idx, ctypes.c_int), _ptr(p_val, ctypes.c_double), _ptr(p_E, ctypes.c_double),
+        st.q, _ptr(coef, ctypes.c_double), ctypes.c_double(st.diag), ctypes.c_double(w.dV),
+        ctypes.c_double(tol), maxit,
+        _ptr(x_src, ctypes.c_double), xf_ptr, xo_ptr,
+        _ptr(iters, ctypes.c_int), _ptr(resid, ctypes.c_double), _ptr(status, ctypes.c_int))
+    xs = (x_src[0::2] + 1j * x_src[1::2]).reshape(n_nodes, P)
+    rho = (2.0 / w.dV) * np.imag(wts[None, :] * xs).sum(axis=1)
+    e_node = 2.0 * np.imag(wts[None, :] * (1.0 + z[None, :] * xs)).sum(axis=1)
+    xf = None
+    if keep_x:
+        xc = x_full[0::2] + 1j * x_full[1::2]
+        xf = []
+        off = 0
+        for r in range(n_nodes):
+            n = int(sizes[r])
+            xf.append(xc[off:off + n * P].reshape(P, n))
+            off += n * P
+    return OracleResult(rho=rho, e_node=e_node, x_src=xs, iters=iters.reshape(n_nodes, P),
+                        resid=resid.reshape(n_nodes, P), status=status.reshape(n_nodes, P),
+                        z=z, wts=wts, regions=regions, x_full=xf)
+
+
+def dL_dV(w, res: OracleResult, a_node, b_node=None) -> np.ndarray:
+    """Gradient of L with respect to the local potential on the grid."""
+    if res.x_full is None:
+        raise ValueError("solve with keep_x=True first")
+    a_node = np.asarray(a_node, dtype=np.float64)
+    b_node = np.zeros_like(a_node) if b_node is None else np.asarray(b_node, dtype=np.float64)
+    g = np.zeros(w.n_grid)
+    for j, reg in enumerate(res.regions):
+        coefs = (2.0 * a_node[j] / w.dV + 2.0 * b_node[j] * res.z) * res.wts   # (P,)
+        contrib = -np.imag((coefs[:, None] * res.x_full[j] ** 2).sum(axis=0))
+        np.add.at(g, reg.gidx, contrib)
+    return g
+
+
+def forces(w, dLdV: np.ndarray) -> np.ndarray:
+    """F_a = -sum_k dL/dV_k dV_k/dR_a (local Gaussian wells only)."""
+    F = np.zeros((len(w.atoms), 3))
+    for a in range(len(w.atoms)):
+        gidx, dVdR = ham_mod.local_potential_gradient_terms(w, a)
+        F[a] = -(dLdV[gidx][:, None] * dVdR).sum(axis=0)
+    return F
