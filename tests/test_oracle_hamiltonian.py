@@ -110,3 +110,20 @@ def test_region_mapping():
     with pytest.raises(ValueError):
         w2 = make_workload("tiny", shape=(10, 12, 14), s=3, periodic=(False, True, True))
         H.region_of(w2, node, 3)
+
+
+def test_nonlocal_operator_spectrum():
+    """For one atom on a grid point the four projectors are orthonormal in
+    the dV inner product, so sum_l E_l dV |p_l><p_l| has eigenvalues
+    exactly {E_s, E_p, E_p, E_p, 0, ...}."""
+    w = _single_atom(shape=(16, 16, 16), h=0.6, R=(4.8, 4.8, 4.8))
+    w.nonlocal_proj = True
+    w.e_s, w.e_p = 0.5, 0.25
+    projs = H.projectors(w)
+    M = np.zeros((w.n_grid, w.n_grid))
+    for p in projs:
+        v = np.zeros(w.n_grid); v[p.idx] = p.val
+        M += p.energy * w.dV * np.outer(v, v)
+    ev = np.sort(np.linalg.eigvalsh(M))[::-1]
+    np.testing.assert_allclose(ev[:4], [0.5, 0.25, 0.25, 0.25], atol=1e-12)
+    assert np.abs(ev[4:]).max() < 1e-12
