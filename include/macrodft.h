@@ -1,0 +1,240 @@
+/*
+ * macrodft.h -- C ABI of the GB300 nodal-density library.
+ *
+ * The library computes the electron density at sampled grid nodes as the
+ * diagonal of the finite-temperature density matrix, rho_p = 2 h^-3
+ * <e_p| g(H) |e_p> (arXiv:1907.02604, Section 2.1, Eqs. (dm) and
+ * (Electron_density:GQ)), with the Fermi-Dirac function g replaced by a
+ * P-pole rational approximation r(eps) = sum_p Im(w_p / (eps - z_p)) and
+ * H replaced by its restriction H_R to a cube around each node (the
+ * locality argument of Section 2.1).  Every (node j, pole z_p) pair is one
+ * complex-symmetric solve (H_R - z_p I) x = e_j done with COCG on the GPU:
+ *
+ *     rho_j = (2/dV) sum_p Im( w_p x_jp(j) )
+ *     e_j   = 2 sum_p Im( w_p (1 + z_p x_jp(j)) )        (band energy)
+ *
+ * Conventions (all entry points):
+ *   - Grid arrays are flat, x fastest: g = ix + nx*(iy + ny*iz).
+ *   - Pointers documented "device" are CUDA device pointers owned by the
+ *     caller; "host" pointers are read during the call only.  The library
+ *     owns only the opaque handles it returns, each with a destroy call.
+ *   - Calls are asynchronous on the given stream (cudaStream_t passed as
+ *     void*, NULL = legacy default stream) unless documented otherwise.
+ *   - On error the call returns a non-zero md_status, launches nothing
+ *     (validation errors) and md_last_error() describes the problem.
+ *   - Complex numbers are interleaved doubles (re, im).
+ *   - Requires an sm_103a GPU; every compute entry point returns
+ *     MD_ERR_CUDA when no such device is present.
+ */
+#ifndef MACRODFT_H
+#define MACRODFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_INVALID = 1,    /* bad argument; nothing launched */
+    MD_ERR_NOCONV = 2,     /* outputs written, some systems hit maxit */
+    MD_ERR_BREAKDOWN = 3,  /* outputs written, some systems broke down (r^T r ~ 0) */
+    MD_ERR_TIMEOUT = 4,    /* device deadline passed; outputs incomplete */
+    MD_ERR_OOM = 5,        /* device allocation failed */
+    MD_ERR_CUDA = 6        /* CUDA runtime error or no usable device */
+} md_status;
+
+typedef enum { MD_PREC_FP64 = 0, MD_PREC_MIXED = 1 } md_precision;
+
+/* Uniform real-space grid (Section 2.1: uniform spacing h, finite
+ * differences of order fd_order).  Spacing may differ per axis; dV =
+ * h[0]*h[1]*h[2] plays the role of the paper's h^3. */
+typedef struct {
+    int32_t n[3];          /* points per axis (x, y, z), each >= 1 */
+    double h[3];           /* spacing, bohr, > 0 */
+    int32_t periodic[3];   /* 1 = periodic axis, 0 = open (Dirichlet) */
+    int32_t fd_order;      /* even, 2..16: 2q-order central Laplacian */
+} md_grid;
+
+/* Atoms carrying Gaussian wells V_a(r) = -depth exp(-|r-R|^2/(2 sigma^2)).
+ * Host arrays, read during md_build_hamiltonian only. */
+typedef struct {
+    int64_t n;
+    const double* xyz;     /* host, 3n, bohr, (x, y, z) per atom */
+    const double* depth;   /* host, n, Ha */
+    const double* sigma;   /* host, n, bohr, > 0 */
+} md_atoms;
+
+/* Potential model: local wells (minimum-image distance on periodic axes,
+ * cut at cutoff_sigmas*sigma), an optional additive grid potential, and an
+ * optional separable nonlocal term sum_{a,l} E_l dV |p_al><p_al| with four
+ * Gaussian projectors per atom (s, p_x, p_y, p_z; g = exp(-r^2/(2
+ * proj_sigma^2)), p_s = C g, p_alpha = C (r_alpha - R_alpha) g, zero beyond
+ * proj_rc, each normalised to dV sum p^2 = 1 on the grid).  The nonlocal
+ * term needs every periodic box length > 2*proj_rc. */
+typedef struct {
+    double cutoff_sigmas;  /* > 0 (8.0 in the shipped workloads) */
+    const double* v_ext;   /* host, N = nx*ny*nz additive potential (Ha) or NULL */
+    int32_t nonlocal;      /* 0 or 1 */
+    double proj_sigma;     /* bohr */
+    double proj_rc;        /* bohr */
+    double e_s;            /* Ha, energy of the s projector */
+    double e_p;            /* Ha, energy of the three p projectors */
+} md_pot_params;
+
+typedef struct md_hamiltonian md_hamiltonian;   /* opaque, device resident */
+typedef struct md_workspace md_workspace;       /* opaque checkpoint of x_jp */
+
+/* Pole set of the rational Fermi approximation (host arrays). */
+typedef struct {
+    int32_t n_poles;       /* P >= 1 */
+    const double* z;       /* host, 2P: poles, Im z > 0 */
+    const double* w;       /* host, 2P: weights */
+} md_poles;
+
+/* Sampled nodes (the paper's electronic sampling points, Section 2.2) and
+ * the half-width s of each node's cubic region: the region is the
+ * (2s+1)^3 cube centred on the node, wrapped on periodic axes; where
+ * 2s+1 >= n on a periodic axis the region spans the whole axis as a ring.
+ * On an open axis the cube must stay inside the grid. */
+typedef struct {
+    int64_t n_nodes;
+    const int64_t* node;       /* host, n_nodes grid indices */
+    const int32_t* halfwidth;  /* host, n_nodes, s >= 0 */
+} md_nodes;
+
+typedef struct {
+    double tol;            /* stop when ||r||_2 <= tol (||e_j|| = 1); > 0 */
+    int32_t maxit;         /* iteration cap per system, > 0 */
+    int32_t precision;     /* md_precision */
+    int32_t reliable_every;/* mixed: max iterations between FP64 residual
+                              recomputations (0 = 200) */
+    double reliable_delta; /* mixed: also recompute when ||r|| fell by this
+                              factor since the last one (0 = 1e-2) */
+    double timeout_s;      /* device wall-clock budget for the call, 0 = none */
+    int32_t block;         /* threads per CTA; 0 = library choice */
+    int32_t ctas_per_sm;   /* resident CTAs per SM; 0 = library choice */
+} md_solver_opts;
+
+/* Per-call statistics, filled (after a stream synchronisation) when the
+ * pointer passed to a compute call is non-NULL. */
+typedef struct {
+    int64_t n_systems;
+    int64_t n_converged;
+    int64_t n_noconv;
+    int64_t n_breakdown;
+    int64_t n_timeout;
+    int32_t iters_min;
+    int32_t iters_max;
+    double iters_mean;
+    int64_t total_iters;       /* sum over systems */
+    int64_t total_point_iters; /* sum over systems of iters * region points */
+    int64_t reliable_updates;  /* mixed: FP64 residual recomputations */
+    double max_resid;          /* max final relative residual */
+    double kernel_ms;          /* device time of the solver launch */
+} md_stats;
+
+/* ---- Hamiltonian (Eq. Hamiltonian, discretised as in Section 2.1) ----- */
+
+/* Builds V on the grid on the device (sum of wells + v_ext), the per-atom
+ * projector normalisations and the per-point projector lists.  *out is
+ * owned by the library; free it with md_hamiltonian_destroy.  Synchronous
+ * with respect to the host for its own allocations; the kernels run on
+ * `stream`.  Errors: MD_ERR_INVALID (bad sizes, non-positive spacing or
+ * sigma, odd fd_order, nonlocal with a periodic box <= 2 proj_rc),
+ * MD_ERR_OOM, MD_ERR_CUDA. */
+md_status md_build_hamiltonian(const md_grid* grid, const md_atoms* atoms,
+                               const md_pot_params* pot, void* stream,
+                               md_hamiltonian** out);
+md_status md_hamiltonian_destroy(md_hamiltonian* ham);
+
+/* Copies V (N doubles) to device memory V_out, stream-ordered. */
+md_status md_hamiltonian_potential(const md_hamiltonian* ham, double* V_out, void* stream);
+
+/* Replaces V by the device array V_in (N doubles), stream-ordered; used to
+ * differentiate with respect to the local potential directly. */
+md_status md_hamiltonian_set_potential(md_hamiltonian* ham, const double* V_in, void* stream);
+
+/* Gershgorin interval [emin, emax] containing the spectrum of H and hence
+ * of every H_R (Cauchy interlacing).  Synchronises `stream`. */
+md_status md_spectral_bounds(const md_hamiltonian* ham, void* stream,
+                             double* emin, double* emax);
+
+/* ---- Poles (host) -------------------------------------------------------
+ * P-pole approximation of g(eps) = 1/(1+exp((eps-mu)/kT)) (Eq. dm) on
+ * [emin, emax]: contour quadrature of Hale, Higham & Trefethen (2008) with
+ * the square-root substitution of Lin, Lu, Ying & E (2009); P must be even.
+ * z_out, w_out: host, 2P doubles each (interleaved complex).  Pure host
+ * code: needs no GPU. */
+md_status md_make_poles(double kT, double mu, double emin, double emax, int32_t P,
+                        double* z_out, double* w_out);
+
+/* ---- Density, band energy, adjoint -------------------------------------- */
+
+/* Checkpoint of all forward solutions x_jp (complex128, one region-sized
+ * vector per system) for md_density_adjoint.  Allocates
+ * 16 * P * sum_j |R(j)| bytes of device memory. */
+md_status md_workspace_create(const md_hamiltonian* ham, const md_nodes* nodes,
+                              int32_t n_poles, md_workspace** out);
+md_status md_workspace_destroy(md_workspace* ws);
+
+/* Nodal density (Eq. Electron_density:GQ with g -> r):
+ *   rho_out: device, n_nodes doubles, rho_j = (2/dV) sum_p Im(w_p x_jp(j)).
+ *   e_out:   device, n_nodes doubles or NULL, e_j = 2 sum_p Im(w_p(1+z_p x_jp(j))).
+ *   ckpt:    NULL, or a workspace made for the same nodes and pole count;
+ *            receives every x_jp.
+ * Returns MD_OK, or MD_ERR_NOCONV / MD_ERR_BREAKDOWN / MD_ERR_TIMEOUT with
+ * the outputs still written (those are known only after synchronising:
+ * the call synchronises `stream` when stats != NULL or when it must report
+ * them, i.e. always in this version). */
+md_status md_density(const md_hamiltonian* ham, const md_poles* poles,
+                     const md_nodes* nodes, const md_solver_opts* opts,
+                     double* rho_out, double* e_out, md_workspace* ckpt,
+                     md_stats* stats, void* stream);
+
+/* Band energy (first term of Eq. tot): e_out per node (device, may be
+ * NULL) and their sum in *e_band (host).  Same solves as md_density. */
+md_status md_energy(const md_hamiltonian* ham, const md_poles* poles,
+                    const md_nodes* nodes, const md_solver_opts* opts,
+                    double* e_out, double* e_band, md_stats* stats, void* stream);
+
+/* Adjoint of (rho, e) -> L.  With a_j = dL/drho_j and b_j = dL/de_j:
+ *   dL/dV_k = -sum_j sum_p Im((2 a_j/dV + 2 b_j z_p) w_p x_jp(k)^2)
+ * (G = (H_R - z)^-1 is complex symmetric, so dG_jj/dV_k = -x_jp(k)^2 and
+ * the adjoint systems are the forward ones), and, when forces_out is
+ * non-NULL, the Hellmann-Feynman forces through the local wells
+ * (Section 2.1, last paragraph):
+ *   F_a = -sum_k dL/dV_k dV_k/dR_a.
+ *   dL_drho: device, n_nodes.  dL_de: device, n_nodes, or NULL (= 0).
+ *   ckpt: workspace filled by md_density with the same inputs, or NULL to
+ *         re-solve the systems here.
+ *   dL_dV_out: device, N doubles (overwritten).
+ *   forces_out: device, 3*n_atoms doubles (overwritten) or NULL; needs a
+ *         Hamiltonian built from atoms without the nonlocal term.
+ * Regions of different nodes overlap, so dL_dV is accumulated with FP64
+ * atomics and its last bits depend on scheduling. */
+md_status md_density_adjoint(const md_hamiltonian* ham, const md_poles* poles,
+                             const md_nodes* nodes, const md_solver_opts* opts,
+                             const double* dL_drho, const double* dL_de,
+                             md_workspace* ckpt, double* dL_dV_out,
+                             double* forces_out, md_stats* stats, void* stream);
+
+/* Central weights w_0..w_q (q = order/2) of d^2/dx^2 on a unit grid with
+ * accuracy order `order` (even, 2..16), by Fornberg's recursion (Math.
+ * Comp. 51 (1988)); the library's Laplacian is -1/2 sum_d w / h_d^2 (the
+ * paper's Section 2.1 uses order 6).  w_out: host, q+1 doubles.  Pure host
+ * code: needs no GPU. */
+md_status md_fd_weights(int32_t order, double* w_out);
+
+/* Description of the last error on the calling host thread ("" if none). */
+const char* md_last_error(void);
+
+/* Library version string. */
+const char* md_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MACRODFT_H */

@@ -1,0 +1,13 @@
+"""GB300 nodal-density library (arXiv:1907.02604, MacroDFT hot path).
+
+Electron density at sampled grid nodes, rho_j = (2/dV) sum_p Im(w_p
+x_jp(j)) with (H_R(j) - z_p) x_jp = e_j solved by COCG in hand-written CUDA
+kernels for sm_103a, behind the C ABI of include/macrodft.h.  This package
+is the Python binding (``api``), the autograd wrapper (``torch_api``) and
+the in-tree build (``build``).
+"""
+from .api import (Hamiltonian, SolverOptions, Workspace, density, density_adjoint, energy,
+                  fd_weights, make_poles)
+
+__all__ = ["Hamiltonian", "SolverOptions", "Workspace", "density", "density_adjoint", "energy",
+           "fd_weights", "make_poles"]

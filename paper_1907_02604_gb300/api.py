@@ -1,0 +1,252 @@
+"""Python front end of the nodal-density library.
+
+Thin marshalling over the C ABI (``_lib``): arguments become C structs and
+raw pointers; PyTorch supplies device memory and the current CUDA stream.
+Every computation runs in the library's CUDA kernels.
+
+    ham = Hamiltonian.from_workload(w)                 # md_build_hamiltonian
+    z, w = make_poles(kT, mu, *ham.spectral_bounds(), P)   # md_make_poles
+    rho, e, stats = density(ham, z, w, nodes, halfwidth)    # md_density
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, load
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_lib.c_double_p)
+
+
+def _stream_handle(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _cuda_f64(t: torch.Tensor, n: int, name: str) -> torch.Tensor:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements")
+    return t.contiguous()
+
+
+def fd_weights(order: int) -> np.ndarray:
+    """Central second-derivative weights w_0..w_q (host code, no GPU)."""
+    out = np.zeros(order // 2 + 1)
+    check(load().md_fd_weights(order, _dptr(out)), "md_fd_weights")
+    return out
+
+
+def make_poles(kT: float, mu: float, emin: float, emax: float, P: int):
+    """Poles and weights (complex128 arrays) of the rational Fermi
+    approximation (host code, no GPU)."""
+    z = np.zeros(2 * P)
+    w = np.zeros(2 * P)
+    check(load().md_make_poles(kT, mu, emin, emax, P, _dptr(z), _dptr(w)), "md_make_poles")
+    return z[0::2] + 1j * z[1::2], w[0::2] + 1j * w[1::2]
+
+
+@dataclass
+class SolverOptions:
+    tol: float = 1e-10
+    maxit: int = 20000
+    precision: str = "fp64"        # "fp64" or "mixed"
+    reliable_every: int = 0
+    reliable_delta: float = 0.0
+    timeout_s: float = 0.0
+    block: int = 0
+    ctas_per_sm: int = 0
+
+    def to_c(self) -> _lib.md_solver_opts:
+        prec = {"fp64": _lib.MD_PREC_FP64, "mixed": _lib.MD_PREC_MIXED}[self.precision]
+        return _lib.md_solver_opts(self.tol, self.maxit, prec, self.reliable_every,
+                                   self.reliable_delta, self.timeout_s, self.block, self.ctas_per_sm)
+
+
+class Hamiltonian:
+    """Device-resident discrete Hamiltonian (md_build_hamiltonian)."""
+
+    def __init__(self, shape, spacing, periodic, fd_order, atoms, depth, sigma,
+                 cutoff_sigmas=8.0, v_ext=None, nonlocal_proj=False, proj_sigma=1.0,
+                 proj_rc=4.0, e_s=0.5, e_p=0.25, stream=None):
+        lib = load()
+        self.shape = tuple(int(n) for n in shape)
+        self.spacing = tuple(float(h) for h in spacing)
+        self.N = int(np.prod(self.shape))
+        self.dV = float(np.prod(self.spacing))
+        self._atoms = np.ascontiguousarray(np.asarray(atoms, dtype=np.float64).reshape(-1, 3))
+        self._depth = np.ascontiguousarray(depth, dtype=np.float64)
+        self._sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        self.n_atoms = len(self._atoms)
+        g = _lib.md_grid((ctypes.c_int32 * 3)(*self.shape), (ctypes.c_double * 3)(*self.spacing),
+                         (ctypes.c_int32 * 3)(*[int(bool(p)) for p in periodic]), int(fd_order))
+        a = _lib.md_atoms(self.n_atoms, _dptr(self._atoms), _dptr(self._depth), _dptr(self._sigma))
+        vext = None if v_ext is None else np.ascontiguousarray(v_ext, dtype=np.float64)
+        if vext is not None and vext.size != self.N:
+            raise ValueError("v_ext must have one value per grid point")
+        pot = _lib.md_pot_params(float(cutoff_sigmas), None if vext is None else _dptr(vext),
+                                 int(bool(nonlocal_proj)), float(proj_sigma), float(proj_rc),
+                                 float(e_s), float(e_p))
+        h = ctypes.c_void_p()
+        check(lib.md_build_hamiltonian(ctypes.byref(g), ctypes.byref(a), ctypes.byref(pot),
+                                       _stream_handle(stream), ctypes.byref(h)), "md_build_hamiltonian")
+        self._h = h
+        self.nonlocal_proj = bool(nonlocal_proj)
+
+    @classmethod
+    def from_workload(cls, w, atoms=None, stream=None) -> "Hamiltonian":
+        return cls(w.shape, w.spacing, w.periodic, w.fd_order,
+                   w.atoms if atoms is None else atoms, w.depth, w.sigma,
+                   cutoff_sigmas=w.cutoff_sigmas, v_ext=w.v_ext, nonlocal_proj=w.nonlocal_proj,
+                   proj_sigma=w.proj_sigma, proj_rc=w.proj_rc, e_s=w.e_s, e_p=w.e_p, stream=stream)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("Hamiltonian was closed")
+        return self._h
+
+    def potential(self, stream=None) -> torch.Tensor:
+        out = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        check(load().md_hamiltonian_potential(self.handle, ctypes.c_void_p(out.data_ptr()),
+                                              _stream_handle(stream)), "md_hamiltonian_potential")
+        return out
+
+    def set_potential(self, V: torch.Tensor, stream=None):
+        V = _cuda_f64(V, self.N, "V")
+        check(load().md_hamiltonian_set_potential(self.handle, ctypes.c_void_p(V.data_ptr()),
+                                                  _stream_handle(stream)), "md_hamiltonian_set_potential")
+
+    def spectral_bounds(self, stream=None):
+        lo, hi = ctypes.c_double(), ctypes.c_double()
+        check(load().md_spectral_bounds(self.handle, _stream_handle(stream), ctypes.byref(lo),
+                                        ctypes.byref(hi)), "md_spectral_bounds")
+        return lo.value, hi.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().md_hamiltonian_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _PoleArgs:
+    def __init__(self, z, w):
+        z = np.asarray(z, dtype=np.complex128)
+        w = np.asarray(w, dtype=np.complex128)
+        self.zf = np.ascontiguousarray(np.stack([z.real, z.imag], axis=1).reshape(-1))
+        self.wf = np.ascontiguousarray(np.stack([w.real, w.imag], axis=1).reshape(-1))
+        self.c = _lib.md_poles(len(z), _dptr(self.zf), _dptr(self.wf))
+        self.P = len(z)
+
+
+class _NodeArgs:
+    def __init__(self, nodes, halfwidth):
+        self.node = np.ascontiguousarray(nodes, dtype=np.int64)
+        self.hw = np.ascontiguousarray(halfwidth, dtype=np.int32)
+        if self.node.shape != self.hw.shape:
+            raise ValueError("nodes and halfwidth must have the same length")
+        self.c = _lib.md_nodes(len(self.node), self.node.ctypes.data_as(_lib.c_int64_p),
+                               self.hw.ctypes.data_as(_lib.c_int32_p))
+        self.n = len(self.node)
+
+
+class Workspace:
+    """Checkpoint of every forward solution x_jp (md_workspace_create)."""
+
+    def __init__(self, ham: Hamiltonian, nodes, halfwidth, n_poles: int):
+        self._nodes = _NodeArgs(nodes, halfwidth)
+        h = ctypes.c_void_p()
+        check(load().md_workspace_create(ham.handle, ctypes.byref(self._nodes.c), int(n_poles),
+                                         ctypes.byref(h)), "md_workspace_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().md_workspace_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_SOFT = (_lib.MD_ERR_NOCONV, _lib.MD_ERR_BREAKDOWN)
+
+
+def density(ham: Hamiltonian, z, w, nodes, halfwidth, opts: SolverOptions = None, energy=False,
+            checkpoint: Workspace = None, out=None, stream=None, strict=True):
+    """rho_j (and e_j) for every node.  Returns (rho, e or None, stats dict).
+
+    With strict=False a non-converged or broken-down system does not raise;
+    its status is in the stats."""
+    opts = opts or SolverOptions()
+    pa, na = _PoleArgs(z, w), _NodeArgs(nodes, halfwidth)
+    rho = out if out is not None else torch.empty(na.n, dtype=torch.float64, device="cuda")
+    e = torch.empty(na.n, dtype=torch.float64, device="cuda") if energy else None
+    st = _lib.md_stats()
+    copts = opts.to_c()
+    status = load().md_density(ham.handle, ctypes.byref(pa.c), ctypes.byref(na.c), ctypes.byref(copts),
+                               ctypes.c_void_p(rho.data_ptr()),
+                               ctypes.c_void_p(e.data_ptr()) if e is not None else None,
+                               checkpoint.handle if checkpoint is not None else None,
+                               ctypes.byref(st), _stream_handle(stream))
+    check(status, "md_density", allow=() if strict else _SOFT)
+    d = st.as_dict()
+    d["status"] = _lib.STATUS_NAMES[status]
+    return rho, e, d
+
+
+def energy(ham: Hamiltonian, z, w, nodes, halfwidth, opts: SolverOptions = None, stream=None):
+    """Band energy per node (device tensor) and its sum (float)."""
+    opts = opts or SolverOptions()
+    pa, na = _PoleArgs(z, w), _NodeArgs(nodes, halfwidth)
+    e = torch.empty(na.n, dtype=torch.float64, device="cuda")
+    eb = ctypes.c_double()
+    st = _lib.md_stats()
+    copts = opts.to_c()
+    check(load().md_energy(ham.handle, ctypes.byref(pa.c), ctypes.byref(na.c), ctypes.byref(copts),
+                           ctypes.c_void_p(e.data_ptr()), ctypes.byref(eb), ctypes.byref(st),
+                           _stream_handle(stream)), "md_energy")
+    return e, eb.value, st.as_dict()
+
+
+def density_adjoint(ham: Hamiltonian, z, w, nodes, halfwidth, dL_drho: torch.Tensor,
+                    dL_de: torch.Tensor = None, opts: SolverOptions = None,
+                    checkpoint: Workspace = None, forces=False, stream=None):
+    """dL/dV on the grid and, optionally, the forces -dL/dR on the atoms."""
+    opts = opts or SolverOptions()
+    pa, na = _PoleArgs(z, w), _NodeArgs(nodes, halfwidth)
+    a = _cuda_f64(dL_drho, na.n, "dL_drho")
+    b = None if dL_de is None else _cuda_f64(dL_de, na.n, "dL_de")
+    g = torch.empty(ham.N, dtype=torch.float64, device="cuda")
+    F = torch.empty(3 * ham.n_atoms, dtype=torch.float64, device="cuda") if forces else None
+    st = _lib.md_stats()
+    copts = opts.to_c()
+    check(load().md_density_adjoint(ham.handle, ctypes.byref(pa.c), ctypes.byref(na.c),
+                                    ctypes.byref(copts), ctypes.c_void_p(a.data_ptr()),
+                                    None if b is None else ctypes.c_void_p(b.data_ptr()),
+                                    checkpoint.handle if checkpoint is not None else None,
+                                    ctypes.c_void_p(g.data_ptr()),
+                                    None if F is None else ctypes.c_void_p(F.data_ptr()),
+                                    ctypes.byref(st), _stream_handle(stream)), "md_density_adjoint")
+    return g, (F.view(-1, 3) if F is not None else None)

@@ -1,0 +1,749 @@
+// C ABI of the library: argument checks, region descriptors, scheduling
+// order, workspace management and kernel launches.  See include/macrodft.h
+// for the contract of each entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "md_adjoint.h"
+#include "md_internal.h"
+#include "md_solver.h"
+
+namespace md {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+md_status set_error(md_status code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+void clear_error() { g_last_error.clear(); }
+
+md_status build_hamiltonian_device(Ham& H, const md_atoms* atoms, const md_pot_params* pot,
+                                   cudaStream_t stream);
+
+// FD weights of d^2/dx^2 with accuracy order 2q by Fornberg's recursion
+// (B. Fornberg, Math. Comp. 51 (1988) 699-706) on the nodes 0, +-1, ..., +-q
+// (h = 1); returns w_0..w_q of the symmetric stencil.
+static void fornberg_second_derivative(int q, double* w_out) {
+    const int np = 2 * q + 1;
+    std::vector<double> x(np);
+    x[0] = 0.0;
+    for (int o = 1; o <= q; ++o) {
+        x[2 * o - 1] = o;
+        x[2 * o] = -o;
+    }
+    const int M = 2;
+    // delta[m][n][nu]
+    std::vector<double> delta((M + 1) * np * np, 0.0);
+    auto D = [&](int m, int n, int nu) -> double& { return delta[(m * np + n) * np + nu]; };
+    D(0, 0, 0) = 1.0;
+    double c1 = 1.0;
+    for (int n = 1; n < np; ++n) {
+        double c2 = 1.0;
+        for (int nu = 0; nu < n; ++nu) {
+            const double c3 = x[n] - x[nu];
+            c2 *= c3;
+            for (int m = 0; m <= std::min(n, M); ++m) {
+                const double prev = D(m, n - 1, nu);
+                const double prevm = m > 0 ? D(m - 1, n - 1, nu) : 0.0;
+                D(m, n, nu) = (x[n] * prev - m * prevm) / c3;
+            }
+        }
+        for (int m = 0; m <= std::min(n, M); ++m) {
+            const double a = m > 0 ? D(m - 1, n - 1, n - 1) : 0.0;
+            const double b = D(m, n - 1, n - 1);
+            D(m, n, n) = (c1 / c2) * (m * a - x[n - 1] * b);
+        }
+        c1 = c2;
+    }
+    w_out[0] = D(2, np - 1, 0);
+    for (int o = 1; o <= q; ++o) w_out[o] = D(2, np - 1, 2 * o - 1);
+}
+
+namespace {
+
+#define MD_TRY_CUDA(expr)                                                                 \
+    do {                                                                                  \
+        cudaError_t _e = (expr);                                                          \
+        if (_e != cudaSuccess) {                                                          \
+            st = (_e == cudaErrorMemoryAllocation) ? MD_ERR_OOM : MD_ERR_CUDA;            \
+            set_error(st, std::string("CUDA: ") + cudaGetErrorString(_e) + " (" #expr ")"); \
+            goto done;                                                                    \
+        }                                                                                 \
+    } while (0)
+
+md_status check_device() {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0)
+        return set_error(MD_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, dev);
+    if (prop.major * 10 + prop.minor < 100)
+        return set_error(MD_ERR_CUDA, "this library is built for sm_103a (Blackwell Ultra)");
+    return MD_OK;
+}
+
+void free_ham(Ham& H) {
+    void* ptrs[] = {H.V, H.V32, H.atom_xyz, H.atom_depth, H.atom_sigma, H.proj_i0, H.proj_len,
+                    H.proj_d, H.proj_g, H.proj_d32, H.proj_g32, H.proj_C, H.proj_absum,
+                    H.proj_C32, H.proj_rows, H.pl_ptr, H.pl_atom, H.scratch};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+struct Regions {
+    std::vector<NodeDesc> desc;
+    std::vector<long long> points;
+    long long total = 0;
+    long long n_max = 0;
+};
+
+md_status make_regions(const Ham& H, const md_nodes* nodes, Regions& R) {
+    if (!nodes || nodes->n_nodes < 0 || (nodes->n_nodes > 0 && (!nodes->node || !nodes->halfwidth)))
+        return set_error(MD_ERR_INVALID, "nodes: null arrays or negative count");
+    const long long nn = nodes->n_nodes;
+    R.desc.resize(nn);
+    R.points.resize(nn);
+    R.total = 0;
+    R.n_max = 0;
+    for (long long j = 0; j < nn; ++j) {
+        const long long g = nodes->node[j];
+        const int s = nodes->halfwidth[j];
+        if (g < 0 || g >= H.N) return set_error(MD_ERR_INVALID, "node index out of range");
+        if (s < 0) return set_error(MD_ERR_INVALID, "negative region half-width");
+        const int c[3] = {(int)(g % H.n[0]), (int)((g / H.n[0]) % H.n[1]),
+                          (int)(g / ((long long)H.n[0] * H.n[1]))};
+        NodeDesc& d = R.desc[j];
+        d.ring = 0;
+        int srcc[3];
+        long long pts = 1;
+        for (int ax = 0; ax < 3; ++ax) {
+            const long long m = 2LL * s + 1;
+            if (H.periodic[ax] && m >= H.n[ax]) {
+                d.dims[ax] = H.n[ax];
+                d.lo[ax] = 0;
+                d.ring |= 1 << ax;
+                srcc[ax] = c[ax];
+            } else {
+                if (!H.periodic[ax] && (c[ax] - s < 0 || c[ax] + s >= H.n[ax]))
+                    return set_error(MD_ERR_INVALID, "region leaves a non-periodic grid axis");
+                d.dims[ax] = (int)m;
+                d.lo[ax] = c[ax] - s;
+                srcc[ax] = s;
+            }
+            pts *= d.dims[ax];
+        }
+        if (pts > (1LL << 30)) return set_error(MD_ERR_INVALID, "region too large");
+        d.src = srcc[0] + d.dims[0] * (srcc[1] + d.dims[1] * srcc[2]);
+        R.points[j] = pts;
+        R.total += pts;
+        R.n_max = std::max(R.n_max, pts);
+    }
+    return MD_OK;
+}
+
+md_status check_poles(const md_poles* poles) {
+    if (!poles || poles->n_poles < 1 || !poles->z || !poles->w)
+        return set_error(MD_ERR_INVALID, "poles: need n_poles >= 1 and z, w");
+    for (int p = 0; p < poles->n_poles; ++p) {
+        if (!std::isfinite(poles->z[2 * p]) || !std::isfinite(poles->z[2 * p + 1]) ||
+            !std::isfinite(poles->w[2 * p]) || !std::isfinite(poles->w[2 * p + 1]))
+            return set_error(MD_ERR_INVALID, "poles: non-finite value");
+        if (!(poles->z[2 * p + 1] > 0.0)) return set_error(MD_ERR_INVALID, "poles: need Im z > 0");
+    }
+    return MD_OK;
+}
+
+md_solver_opts normalise_opts(const md_solver_opts* o) {
+    md_solver_opts r;
+    std::memset(&r, 0, sizeof(r));
+    if (o) r = *o;
+    if (r.reliable_every <= 0) r.reliable_every = 200;
+    if (!(r.reliable_delta > 0.0)) r.reliable_delta = 1e-2;
+    return r;
+}
+
+md_status check_opts(const md_solver_opts* o) {
+    if (!o) return set_error(MD_ERR_INVALID, "opts is NULL");
+    if (!(o->tol > 0.0) || o->maxit <= 0)
+        return set_error(MD_ERR_INVALID, "opts: need tol > 0 and maxit > 0");
+    if (o->precision != MD_PREC_FP64 && o->precision != MD_PREC_MIXED)
+        return set_error(MD_ERR_INVALID, "opts: unknown precision");
+    if (o->block != 0 && (o->block < 64 || o->block > 1024 || o->block % 32))
+        return set_error(MD_ERR_INVALID, "opts: block must be a multiple of 32 in [64, 1024]");
+    return MD_OK;
+}
+
+// Solve every (node, pole) system; outputs x_src (device, n_nodes*P).
+md_status run_solver(Ham& H, const md_poles* poles, const Regions& R, const md_solver_opts* opts_in,
+                     double2* d_xsrc, md_workspace* ckpt, md_stats* stats, cudaStream_t stream,
+                     const double2* d_z) {
+    md_status st = MD_OK;
+    const md_solver_opts opts = normalise_opts(opts_in);
+    const int Pn = poles->n_poles;
+    const long long nn = (long long)R.desc.size();
+    const long long n_sys = nn * Pn;
+    int dev = 0, n_sm = 0;
+    SysDesc* d_sys = nullptr;
+    NodeDesc* d_nodes = nullptr;
+    long long* d_ckoff = nullptr;
+    int* d_status = nullptr;
+    int* d_iters = nullptr;
+    int* d_nrel = nullptr;
+    double* d_resid = nullptr;
+    unsigned int* d_counter = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<SysDesc> sys;
+    std::vector<long long> ckoff;
+    std::vector<int> h_status, h_iters, h_nrel;
+    std::vector<double> h_resid;
+    SolveParams P;
+    int block, per_sm, grid;
+    size_t slot, need;
+    long long n_max_r;
+    float ms = 0.f;
+    std::memset(&P, 0, sizeof(P));
+    if (n_sys == 0) {
+        if (stats) {
+            std::memset(stats, 0, sizeof(*stats));
+        }
+        return MD_OK;
+    }
+    if (n_sys > (1LL << 31) - 1) return set_error(MD_ERR_INVALID, "too many systems");
+    MD_TRY_CUDA(cudaGetDevice(&dev));
+    MD_TRY_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+
+    // scheduling order: big regions first, then poles nearest the real axis
+    sys.resize(n_sys);
+    for (long long j = 0; j < nn; ++j)
+        for (int p = 0; p < Pn; ++p) sys[j * Pn + p] = SysDesc{(int)j, p};
+    std::stable_sort(sys.begin(), sys.end(), [&](const SysDesc& a, const SysDesc& b) {
+        const double ca = (double)R.points[a.node] / std::sqrt(poles->z[2 * a.pole + 1]);
+        const double cb = (double)R.points[b.node] / std::sqrt(poles->z[2 * b.pole + 1]);
+        return ca > cb;
+    });
+    if (ckpt) {
+        ckoff.resize(n_sys);
+        for (long long j = 0; j < nn; ++j)
+            for (int p = 0; p < Pn; ++p) ckoff[j * Pn + p] = Pn * ckpt->node_off[j] + p * R.points[j];
+    }
+
+    block = opts.block > 0 ? opts.block : 512;
+    per_sm = opts.ctas_per_sm > 0 ? opts.ctas_per_sm : std::max(1, 1024 / block);
+    grid = (int)std::min<long long>((long long)n_sm * per_sm, n_sys);
+    n_max_r = (R.n_max + 63) / 64 * 64;
+    slot = slot_bytes_for(opts.precision, R.n_max);
+    need = slot * (size_t)grid;
+    if (need > H.scratch_bytes) {
+        if (H.scratch) cudaFree(H.scratch);
+        H.scratch = nullptr;
+        H.scratch_bytes = 0;
+        MD_TRY_CUDA(cudaMalloc(&H.scratch, need));
+        H.scratch_bytes = need;
+    }
+    MD_TRY_CUDA(cudaMallocAsync((void**)&d_sys, n_sys * sizeof(SysDesc), stream));
+    MD_TRY_CUDA(cudaMallocAsync((void**)&d_nodes, nn * sizeof(NodeDesc), stream));
+    MD_TRY_CUDA(cudaMallocAsync((void**)&d_status, n_sys * sizeof(int), stream));
+    MD_TRY_CUDA(cudaMallocAsync((void**)&d_iters, n_sys * sizeof(int), stream));
+    MD_TRY_CUDA(cudaMallocAsync((void**)&d_nrel, n_sys * sizeof(int), stream));
+    MD_TRY_CUDA(cudaMallocAsync((void**)&d_resid, n_sys * sizeof(double), stream));
+    MD_TRY_CUDA(cudaMallocAsync((void**)&d_counter, sizeof(unsigned int), stream));
+    MD_TRY_CUDA(cudaMemcpyAsync(d_sys, sys.data(), n_sys * sizeof(SysDesc), cudaMemcpyHostToDevice, stream));
+    MD_TRY_CUDA(cudaMemcpyAsync(d_nodes, R.desc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, stream));
+    MD_TRY_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream));
+    if (ckpt) {
+        MD_TRY_CUDA(cudaMallocAsync((void**)&d_ckoff, n_sys * sizeof(long long), stream));
+        MD_TRY_CUDA(cudaMemcpyAsync(d_ckoff, ckoff.data(), n_sys * sizeof(long long), cudaMemcpyHostToDevice, stream));
+    }
+
+    for (int d = 0; d < 3; ++d) {
+        P.n[d] = H.n[d];
+        P.periodic[d] = H.periodic[d];
+        for (int o = 0; o < kMaxQ; ++o) P.coef[d][o] = H.coef[d][o];
+    }
+    P.N = H.N;
+    P.q = H.q;
+    P.diag = H.diag;
+    P.dV = H.dV;
+    P.V = H.V;
+    P.V32 = H.V32;
+    P.nonlocal = H.nonlocal && H.n_atoms > 0;
+    P.n_atoms = H.n_atoms;
+    P.proj_i0 = H.proj_i0;
+    P.proj_len = H.proj_len;
+    P.proj_d = H.proj_d;
+    P.proj_g = H.proj_g;
+    P.proj_d32 = H.proj_d32;
+    P.proj_g32 = H.proj_g32;
+    P.proj_C = H.proj_C;
+    P.proj_C32 = H.proj_C32;
+    P.proj_rows = H.proj_rows;
+    P.pl_ptr = H.pl_ptr;
+    P.pl_atom = H.pl_atom;
+    P.e_s = H.e_s;
+    P.e_p = H.e_p;
+    P.n_sys = (int)n_sys;
+    P.P = Pn;
+    P.sys = d_sys;
+    P.nodes = d_nodes;
+    P.z = d_z;
+    P.tol = opts.tol;
+    P.maxit = opts.maxit;
+    P.reliable_every = opts.reliable_every;
+    P.reliable_delta = opts.reliable_delta;
+    P.timeout_ns = opts.timeout_s > 0 ? (unsigned long long)(opts.timeout_s * 1e9) : 0ULL;
+    P.scratch = (char*)H.scratch;
+    P.slot_bytes = slot;
+    P.n_max = (int)n_max_r;
+    P.ckpt = ckpt ? (double2*)ckpt->x : nullptr;
+    P.ckpt_sys_off = d_ckoff;
+    P.work_counter = d_counter;
+    P.x_src = d_xsrc;
+    P.status = d_status;
+    P.iters = d_iters;
+    P.resid = d_resid;
+    P.n_rel = d_nrel;
+
+    MD_TRY_CUDA(cudaEventCreate(&ev0));
+    MD_TRY_CUDA(cudaEventCreate(&ev1));
+    MD_TRY_CUDA(cudaEventRecord(ev0, stream));
+    MD_TRY_CUDA(launch_cocg(P, opts.precision, grid, block, stream));
+    MD_TRY_CUDA(cudaEventRecord(ev1, stream));
+
+    h_status.resize(n_sys);
+    h_iters.resize(n_sys);
+    h_nrel.resize(n_sys);
+    h_resid.resize(n_sys);
+    MD_TRY_CUDA(cudaMemcpyAsync(h_status.data(), d_status, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    MD_TRY_CUDA(cudaMemcpyAsync(h_iters.data(), d_iters, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    MD_TRY_CUDA(cudaMemcpyAsync(h_nrel.data(), d_nrel, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    MD_TRY_CUDA(cudaMemcpyAsync(h_resid.data(), d_resid, n_sys * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    MD_TRY_CUDA(cudaStreamSynchronize(stream));
+    MD_TRY_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+    {
+        md_stats sst;
+        std::memset(&sst, 0, sizeof(sst));
+        sst.n_systems = n_sys;
+        sst.iters_min = 1 << 30;
+        for (long long k = 0; k < n_sys; ++k) {
+            const int s = h_status[k];
+            if (s == 0) sst.n_converged++;
+            else if (s == 2) sst.n_noconv++;
+            else if (s == 3) sst.n_breakdown++;
+            else if (s == 4) sst.n_timeout++;
+            sst.iters_min = std::min(sst.iters_min, h_iters[k]);
+            sst.iters_max = std::max(sst.iters_max, h_iters[k]);
+            sst.total_iters += h_iters[k];
+            sst.total_point_iters += (long long)h_iters[k] * R.points[k / Pn];
+            sst.reliable_updates += h_nrel[k];
+            sst.max_resid = std::max(sst.max_resid, h_resid[k]);
+        }
+        sst.iters_mean = (double)sst.total_iters / (double)n_sys;
+        sst.kernel_ms = ms;
+        if (stats) *stats = sst;
+        bool invalid = false;
+        for (long long k = 0; k < n_sys; ++k) invalid = invalid || h_status[k] == 1;
+        if (invalid) {
+            st = set_error(MD_ERR_INVALID, "a region meets more projector atoms than the solver holds (256)");
+        } else if (sst.n_timeout) {
+            st = set_error(MD_ERR_TIMEOUT, "device time budget exhausted; outputs incomplete");
+        } else if (sst.n_breakdown) {
+            st = set_error(MD_ERR_BREAKDOWN, "COCG breakdown (r^T r ~ 0) in some systems");
+        } else if (sst.n_noconv) {
+            st = set_error(MD_ERR_NOCONV, "some systems reached maxit");
+        }
+    }
+done:
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    cudaFreeAsync(d_sys, stream);
+    cudaFreeAsync(d_nodes, stream);
+    cudaFreeAsync(d_status, stream);
+    cudaFreeAsync(d_iters, stream);
+    cudaFreeAsync(d_nrel, stream);
+    cudaFreeAsync(d_resid, stream);
+    cudaFreeAsync(d_counter, stream);
+    if (d_ckoff) cudaFreeAsync(d_ckoff, stream);
+    return st;
+}
+
+md_status upload_poles(const md_poles* poles, double2** d_z, double2** d_w, cudaStream_t stream) {
+    const int Pn = poles->n_poles;
+    cudaError_t e = cudaMallocAsync((void**)d_z, Pn * sizeof(double2), stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)d_w, Pn * sizeof(double2), stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(*d_z, poles->z, Pn * sizeof(double2), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(*d_w, poles->w, Pn * sizeof(double2), cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    return MD_OK;
+}
+
+md_status density_impl(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,
+                       const md_solver_opts* opts, double* rho_out, double* e_out, md_workspace* ckpt,
+                       md_stats* stats, cudaStream_t stream) {
+    md_status st = check_device();
+    if (st != MD_OK) return st;
+    if (!ham) return set_error(MD_ERR_INVALID, "ham is NULL");
+    if ((st = check_poles(poles)) != MD_OK) return st;
+    if ((st = check_opts(opts)) != MD_OK) return st;
+    Ham& H = const_cast<md_hamiltonian*>(ham)->h;
+    Regions R;
+    if ((st = make_regions(H, nodes, R)) != MD_OK) return st;
+    if (!rho_out && R.desc.size() > 0) return set_error(MD_ERR_INVALID, "rho_out is NULL");
+    if (ckpt) {
+        if (ckpt->n_nodes != (long long)R.desc.size() || ckpt->n_poles != poles->n_poles ||
+            ckpt->total_points != R.total)
+            return set_error(MD_ERR_INVALID, "checkpoint workspace was made for other nodes or poles");
+    }
+    const long long nn = (long long)R.desc.size();
+    if (nn == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return MD_OK;
+    }
+    double2* d_z = nullptr;
+    double2* d_w = nullptr;
+    double2* d_xsrc = nullptr;
+    md_status st2 = MD_OK;
+    if ((st = upload_poles(poles, &d_z, &d_w, stream)) != MD_OK) goto done;
+    MD_TRY_CUDA(cudaMallocAsync((void**)&d_xsrc, nn * poles->n_poles * sizeof(double2), stream));
+    st2 = run_solver(H, poles, R, opts, d_xsrc, ckpt, stats, stream, d_z);
+    if (st2 == MD_OK || st2 == MD_ERR_NOCONV || st2 == MD_ERR_BREAKDOWN || st2 == MD_ERR_TIMEOUT) {
+        MD_TRY_CUDA(launch_accumulate((int)nn, poles->n_poles, d_xsrc, d_z, d_w, H.dV, rho_out, e_out, stream));
+    }
+    st = st2;
+done:
+    cudaFreeAsync(d_z, stream);
+    cudaFreeAsync(d_w, stream);
+    cudaFreeAsync(d_xsrc, stream);
+    return st;
+}
+
+}  // namespace
+}  // namespace md
+
+using namespace md;
+
+extern "C" {
+
+const char* md_last_error(void) { return md::g_last_error.c_str(); }
+
+const char* md_version(void) { return "macrodft-gb300 0.1 (sm_103a)"; }
+
+md_status md_make_poles(double kT, double mu, double emin, double emax, int32_t P, double* z_out,
+                        double* w_out) {
+    clear_error();
+    return make_poles(kT, mu, emin, emax, P, z_out, w_out);
+}
+
+md_status md_build_hamiltonian(const md_grid* grid, const md_atoms* atoms, const md_pot_params* pot,
+                               void* stream, md_hamiltonian** out) {
+    clear_error();
+    if (!out) return set_error(MD_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!grid || !atoms || !pot) return set_error(MD_ERR_INVALID, "grid, atoms and pot are required");
+    for (int d = 0; d < 3; ++d) {
+        if (grid->n[d] < 1) return set_error(MD_ERR_INVALID, "grid: need n >= 1 on every axis");
+        if (!(grid->h[d] > 0.0) || !std::isfinite(grid->h[d]))
+            return set_error(MD_ERR_INVALID, "grid: spacing must be positive");
+    }
+    if (grid->fd_order < 2 || grid->fd_order > 2 * kMaxQ || grid->fd_order % 2)
+        return set_error(MD_ERR_INVALID, "grid: fd_order must be even, 2..16");
+    if (atoms->n < 0 || (atoms->n > 0 && (!atoms->xyz || !atoms->depth || !atoms->sigma)))
+        return set_error(MD_ERR_INVALID, "atoms: null arrays");
+    for (long long a = 0; a < atoms->n; ++a) {
+        if (!(atoms->sigma[a] > 0.0) || !std::isfinite(atoms->depth[a]) ||
+            !std::isfinite(atoms->xyz[3 * a]) || !std::isfinite(atoms->xyz[3 * a + 1]) ||
+            !std::isfinite(atoms->xyz[3 * a + 2]))
+            return set_error(MD_ERR_INVALID, "atoms: need finite positions/depths and sigma > 0");
+    }
+    if (!(pot->cutoff_sigmas > 0.0)) return set_error(MD_ERR_INVALID, "pot: cutoff_sigmas must be > 0");
+    const long long N = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+    if (pot->v_ext)
+        for (long long i = 0; i < N; ++i)
+            if (!std::isfinite(pot->v_ext[i])) return set_error(MD_ERR_INVALID, "pot: non-finite v_ext");
+    if (pot->nonlocal) {
+        if (!(pot->proj_sigma > 0.0) || !(pot->proj_rc > 0.0))
+            return set_error(MD_ERR_INVALID, "pot: projector sigma and cutoff must be > 0");
+        for (int d = 0; d < 3; ++d) {
+            if (grid->periodic[d] && !(grid->n[d] * grid->h[d] > 2.0 * pot->proj_rc))
+                return set_error(MD_ERR_INVALID, "pot: nonlocal needs every periodic box length > 2 proj_rc");
+            if (2.0 * std::floor(pot->proj_rc / grid->h[d]) + 2 > kMaxProjWin)
+                return set_error(MD_ERR_INVALID, "pot: proj_rc / h too large for the projector window");
+        }
+    }
+    md_status st = check_device();
+    if (st != MD_OK) return st;
+    md_hamiltonian* hp = new md_hamiltonian();
+    Ham& H = hp->h;
+    for (int d = 0; d < 3; ++d) {
+        H.n[d] = grid->n[d];
+        H.h[d] = grid->h[d];
+        H.periodic[d] = grid->periodic[d] ? 1 : 0;
+    }
+    H.fd_order = grid->fd_order;
+    H.q = grid->fd_order / 2;
+    H.N = N;
+    H.dV = H.h[0] * H.h[1] * H.h[2];
+    cudaGetDevice(&H.device);
+    {
+        double w[kMaxQ + 1];
+        fornberg_second_derivative(H.q, w);
+        H.diag = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double h2 = H.h[d] * H.h[d];
+            for (int o = 0; o < kMaxQ; ++o) H.coef[d][o] = o < H.q ? -0.5 * w[o + 1] / h2 : 0.0;
+            H.diag += -0.5 * w[0] / h2;
+        }
+    }
+    H.n_atoms = atoms->n;
+    H.cutoff_sigmas = pot->cutoff_sigmas;
+    H.nonlocal = pot->nonlocal ? 1 : 0;
+    H.proj_sigma = pot->proj_sigma;
+    H.proj_rc = pot->proj_rc;
+    H.e_s = pot->e_s;
+    H.e_p = pot->e_p;
+    st = build_hamiltonian_device(H, atoms, pot, (cudaStream_t)stream);
+    if (st != MD_OK) {
+        free_ham(H);
+        delete hp;
+        return st;
+    }
+    *out = hp;
+    return MD_OK;
+}
+
+md_status md_hamiltonian_destroy(md_hamiltonian* ham) {
+    clear_error();
+    if (!ham) return MD_OK;
+    free_ham(ham->h);
+    delete ham;
+    return MD_OK;
+}
+
+md_status md_hamiltonian_potential(const md_hamiltonian* ham, double* V_out, void* stream) {
+    clear_error();
+    if (!ham || !V_out) return set_error(MD_ERR_INVALID, "ham and V_out are required");
+    cudaError_t e = cudaMemcpyAsync(V_out, ham->h.V, ham->h.N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_error(MD_ERR_CUDA, cudaGetErrorString(e));
+    return MD_OK;
+}
+
+md_status md_spectral_bounds(const md_hamiltonian* ham, void* stream, double* emin, double* emax) {
+    clear_error();
+    if (!ham || !emin || !emax) return set_error(MD_ERR_INVALID, "ham, emin and emax are required");
+    Ham& H = const_cast<md_hamiltonian*>(ham)->h;
+    if (!H.bounds_valid) {
+        md_status st = compute_bounds(H, stream);
+        if (st != MD_OK) return st;
+    }
+    *emin = H.emin;
+    *emax = H.emax;
+    return MD_OK;
+}
+
+md_status md_workspace_create(const md_hamiltonian* ham, const md_nodes* nodes, int32_t n_poles,
+                              md_workspace** out) {
+    clear_error();
+    if (!out) return set_error(MD_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!ham || n_poles < 1) return set_error(MD_ERR_INVALID, "ham and n_poles >= 1 are required");
+    Regions R;
+    md_status st = make_regions(ham->h, nodes, R);
+    if (st != MD_OK) return st;
+    md_workspace* ws = new md_workspace();
+    ws->device = ham->h.device;
+    ws->n_nodes = (long long)R.desc.size();
+    ws->n_poles = n_poles;
+    ws->total_points = R.total;
+    ws->node_off = new long long[std::max<long long>(ws->n_nodes, 1)];
+    long long off = 0;
+    for (long long j = 0; j < ws->n_nodes; ++j) {
+        ws->node_off[j] = off;
+        off += R.points[j];
+    }
+    ws->x = nullptr;
+    const size_t bytes = (size_t)n_poles * (size_t)std::max<long long>(R.total, 1) * 16;
+    cudaError_t e = cudaMalloc((void**)&ws->x, bytes);
+    if (e != cudaSuccess) {
+        delete[] ws->node_off;
+        delete ws;
+        return set_error(e == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA,
+                         std::string("workspace: ") + cudaGetErrorString(e));
+    }
+    *out = ws;
+    return MD_OK;
+}
+
+md_status md_workspace_destroy(md_workspace* ws) {
+    clear_error();
+    if (!ws) return MD_OK;
+    cudaFree(ws->x);
+    delete[] ws->node_off;
+    delete ws;
+    return MD_OK;
+}
+
+md_status md_density(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,
+                     const md_solver_opts* opts, double* rho_out, double* e_out, md_workspace* ckpt,
+                     md_stats* stats, void* stream) {
+    clear_error();
+    return density_impl(ham, poles, nodes, opts, rho_out, e_out, ckpt, stats, (cudaStream_t)stream);
+}
+
+md_status md_energy(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,
+                    const md_solver_opts* opts, double* e_out, double* e_band, md_stats* stats,
+                    void* stream) {
+    clear_error();
+    if (!e_band) return set_error(MD_ERR_INVALID, "e_band is NULL");
+    if (!nodes) return set_error(MD_ERR_INVALID, "nodes is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long nn = nodes->n_nodes;
+    double* d_rho = nullptr;
+    double* d_e = e_out;
+    md_status st = MD_OK;
+    std::vector<double> h_e(std::max<long long>(nn, 1));
+    double sum = 0.0;
+    if (nn <= 0) {
+        *e_band = 0.0;
+        return MD_OK;
+    }
+    MD_TRY_CUDA(cudaMallocAsync((void**)&d_rho, nn * sizeof(double), s));
+    if (!d_e) MD_TRY_CUDA(cudaMallocAsync((void**)&d_e, nn * sizeof(double), s));
+    st = density_impl(ham, poles, nodes, opts, d_rho, d_e, nullptr, stats, s);
+    if (st == MD_ERR_INVALID || st == MD_ERR_CUDA || st == MD_ERR_OOM) goto done;
+    {
+        cudaError_t e1 = cudaMemcpyAsync(h_e.data(), d_e, nn * sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            st = set_error(MD_ERR_CUDA, "copy of node energies failed");
+            goto done;
+        }
+        for (long long j = 0; j < nn; ++j) sum += h_e[j];
+        *e_band = sum;
+    }
+done:
+    cudaFreeAsync(d_rho, s);
+    if (!e_out && d_e) cudaFreeAsync(d_e, s);
+    return st;
+}
+
+md_status md_density_adjoint(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,
+                             const md_solver_opts* opts, const double* dL_drho, const double* dL_de,
+                             md_workspace* ckpt, double* dL_dV_out, double* forces_out, md_stats* stats,
+                             void* stream) {
+    clear_error();
+    md_status st = check_device();
+    if (st != MD_OK) return st;
+    if (!ham || !dL_dV_out) return set_error(MD_ERR_INVALID, "ham and dL_dV_out are required");
+    if ((st = check_poles(poles)) != MD_OK) return st;
+    Ham& H = const_cast<md_hamiltonian*>(ham)->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    Regions R;
+    if ((st = make_regions(H, nodes, R)) != MD_OK) return st;
+    if (!dL_drho && R.desc.size() > 0) return set_error(MD_ERR_INVALID, "dL_drho is NULL");
+    if (forces_out && H.nonlocal && H.n_atoms > 0)
+        return set_error(MD_ERR_INVALID, "forces need a Hamiltonian without the nonlocal term");
+    if (forces_out && H.n_atoms == 0) return set_error(MD_ERR_INVALID, "forces need atoms");
+    md_workspace* own = nullptr;
+    NodeDesc* d_nodes = nullptr;
+    long long* d_off = nullptr;
+    double2* d_z = nullptr;
+    double2* d_w = nullptr;
+    const long long nn = (long long)R.desc.size();
+    md_status solve_st = MD_OK;
+    AdjointParams A;
+    std::memset(&A, 0, sizeof(A));
+    if (!ckpt) {
+        if ((st = check_opts(opts)) != MD_OK) return st;
+        if ((st = md_workspace_create(ham, nodes, poles->n_poles, &own)) != MD_OK) return st;
+        ckpt = own;
+        std::vector<double> dummy;
+        double* d_rho = nullptr;
+        cudaMallocAsync((void**)&d_rho, std::max<long long>(nn, 1) * sizeof(double), s);
+        solve_st = density_impl(ham, poles, nodes, opts, d_rho, nullptr, ckpt, stats, s);
+        cudaFreeAsync(d_rho, s);
+        if (solve_st == MD_ERR_INVALID || solve_st == MD_ERR_CUDA || solve_st == MD_ERR_OOM ||
+            solve_st == MD_ERR_TIMEOUT) {
+            st = solve_st;
+            goto done;
+        }
+    } else if (ckpt->n_nodes != nn || ckpt->n_poles != poles->n_poles || ckpt->total_points != R.total) {
+        return set_error(MD_ERR_INVALID, "checkpoint workspace was made for other nodes or poles");
+    }
+    MD_TRY_CUDA(cudaMemsetAsync(dL_dV_out, 0, H.N * sizeof(double), s));
+    if (nn > 0) {
+        if ((st = upload_poles(poles, &d_z, &d_w, s)) != MD_OK) goto done;
+        MD_TRY_CUDA(cudaMallocAsync((void**)&d_nodes, nn * sizeof(NodeDesc), s));
+        MD_TRY_CUDA(cudaMallocAsync((void**)&d_off, nn * sizeof(long long), s));
+        MD_TRY_CUDA(cudaMemcpyAsync(d_nodes, R.desc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, s));
+        MD_TRY_CUDA(cudaMemcpyAsync(d_off, ckpt->node_off, nn * sizeof(long long), cudaMemcpyHostToDevice, s));
+        for (int d = 0; d < 3; ++d) A.n[d] = H.n[d];
+        A.n_nodes = nn;
+        A.P = poles->n_poles;
+        A.nodes = d_nodes;
+        A.node_off = d_off;
+        A.ckpt = (const double2*)ckpt->x;
+        A.z = d_z;
+        A.w = d_w;
+        A.dL_drho = dL_drho;
+        A.dL_de = dL_de;
+        A.dV = H.dV;
+        A.dLdV = dL_dV_out;
+        MD_TRY_CUDA(launch_adjoint_dV(A, s));
+    }
+    if (forces_out) {
+        ForceParams F;
+        for (int d = 0; d < 3; ++d) {
+            F.n[d] = H.n[d];
+            F.h[d] = H.h[d];
+            F.periodic[d] = H.periodic[d];
+        }
+        F.n_atoms = H.n_atoms;
+        F.xyz = H.atom_xyz;
+        F.depth = H.atom_depth;
+        F.sigma = H.atom_sigma;
+        F.cutoff_sigmas = H.cutoff_sigmas;
+        F.dLdV = dL_dV_out;
+        F.forces = forces_out;
+        MD_TRY_CUDA(launch_forces(F, s));
+    }
+    MD_TRY_CUDA(cudaStreamSynchronize(s));
+    st = solve_st;
+done:
+    cudaFreeAsync(d_nodes, s);
+    cudaFreeAsync(d_off, s);
+    cudaFreeAsync(d_z, s);
+    cudaFreeAsync(d_w, s);
+    if (own) {
+        cudaStreamSynchronize(s);
+        md_workspace_destroy(own);
+    }
+    return st;
+}
+
+md_status md_hamiltonian_set_potential(md_hamiltonian* ham, const double* V_in, void* stream) {
+    clear_error();
+    if (!ham || !V_in) return set_error(MD_ERR_INVALID, "ham and V_in are required");
+    return set_potential_device(ham->h, V_in, stream);
+}
+
+md_status md_fd_weights(int32_t order, double* w_out) {
+    clear_error();
+    if (order < 2 || order > 2 * kMaxQ || order % 2 || !w_out)
+        return set_error(MD_ERR_INVALID, "md_fd_weights: order must be even, 2..16");
+    fornberg_second_derivative(order / 2, w_out);
+    return MD_OK;
+}
+
+}  // extern "C"

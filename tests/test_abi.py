@@ -1,0 +1,83 @@
+"""The C ABI library builds, loads and exports every declared symbol, and
+its host-only entry points agree with the oracle (no GPU needed)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from tests.oracle_pins_helpers import golden_fd_weights
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "macrodft.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1907_02604_gb300 import build
+    build.build()
+    from paper_1907_02604_gb300 import _lib
+    return _lib.load()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(md_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_boundary():
+    syms = declared_symbols()
+    for name in ["md_build_hamiltonian", "md_density", "md_density_adjoint", "md_energy",
+                 "md_make_poles", "md_spectral_bounds", "md_last_error"]:
+        assert name in syms
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1907_02604_gb300 import _lib
+    bound = {n for n, _, _ in _lib.SIGNATURES}
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+        assert name in bound, f"{name} has no ctypes signature"
+
+
+def test_fd_weights_match_fornberg_table(lib):
+    from paper_1907_02604_gb300 import fd_weights
+    for order, w in golden_fd_weights().items():
+        np.testing.assert_allclose(fd_weights(order), w, rtol=0, atol=1e-14)
+
+
+def test_fd_weights_exact_on_polynomials(lib):
+    from paper_1907_02604_gb300 import fd_weights
+    for order in (10, 12, 14, 16):
+        w = fd_weights(order)
+        q = order // 2
+        for k in range(0, order + 2):
+            terms = [w[0] * 0.3 ** k] + [w[o] * ((0.3 + o) ** k + (0.3 - o) ** k) for o in range(1, q + 1)]
+            exact = k * (k - 1) * 0.3 ** (k - 2) if k >= 2 else 0.0
+            scale = sum(abs(t) for t in terms) + abs(exact)
+            assert abs(sum(terms) - exact) < 1e-12 * scale
+
+
+@pytest.mark.parametrize("P", [2, 8, 16, 32, 64])
+@pytest.mark.parametrize("bounds", [(-3.04, 31.97), (-2.5, 44.0), (0.1, 0.5)])
+def test_make_poles_matches_oracle(lib, P, bounds):
+    from paper_1907_02604_gb300 import make_poles
+    from oracle.poles import fermi_poles
+    z, w = make_poles(0.01, 0.2, bounds[0], bounds[1], P)
+    zo, wo = fermi_poles(0.01, 0.2, bounds[0], bounds[1], P)
+    np.testing.assert_allclose(z, zo, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(w, wo, rtol=1e-10, atol=1e-14 * np.abs(wo).max())
+
+
+def test_make_poles_rejects_bad_input(lib):
+    from paper_1907_02604_gb300 import make_poles
+    from paper_1907_02604_gb300._lib import MacroDFTError
+    for args in [(0.01, 0.2, -1.0, 1.0, 7), (0.0, 0.2, -1.0, 1.0, 8), (0.01, 0.2, 1.0, -1.0, 8)]:
+        with pytest.raises(MacroDFTError):
+            make_poles(*args)
+
+
+def test_version_and_error_string(lib):
+    assert b"sm_103a" in lib.md_version()
+    assert isinstance(lib.md_last_error(), bytes)
