@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the nodal-density hot path on GB300.
+
+One step = one pass of the path over one batch of nodes of the bulk
+workload (1,024-atom hcp Mg-like cell, 96x96x160 grid, 8th-order FD,
+Gaussian projectors, P = 16 poles, 33^3 regions, mixed precision): Fermi
+poles on the spectral interval, the cost-sorted work list, every
+(node, pole) COCG solve, and the pole-weighted density and band-energy
+accumulation.  Successive steps take successive node batches of the
+workload (4,096 nodes in all).
+
+Prints one JSON line (rank 0):
+  value    (node, pole) solves/s over the timed steps, device-resident
+           inputs (Hamiltonian built before the timed region);
+  e2e      the same metric through the C ABI from host buffers: every step
+           builds the Hamiltonian from host arrays, solves, and copies rho
+           and e back to the host;
+  roofline HBM roofline of the solver kernel: algorithmic bytes (80 B per
+           region point per COCG iteration in mixed mode, 160 B in FP64)
+           / the kernel's CUDA-event time, against the measured copy
+           bandwidth;
+  cpu_baseline  the FP64 oracle (plain C, OpenMP) on a bounded sample.
+--impl reference times the oracle itself as the reference arm.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "(node,pole) solves/sec and density nodes/sec at rel err<=1e-6; matvec HBM GB/s"
+BYTES_PER_POINT_ITER = {"mixed": 80.0, "fp64": 160.0}
+FLOPS_PER_POINT_ITER_8TH = 200.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bulk_mixed")
+    ap.add_argument("--nodes-per-step", type=int, default=256)
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    return ap.parse_args()
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def cpu_oracle_sample(w, target_s=15.0):
+    """Time the oracle on a bounded sample of nodes (all poles each)."""
+    from oracle import density as od
+    H = od.build(w)
+    n_done, t_used, solves = 0, 0.0, 0
+    order = np.arange(len(w.nodes))
+    k = 1
+    while t_used < target_s and n_done < len(order):
+        take = order[n_done:n_done + k]
+        sub = w.subset(take)
+        t0 = time.perf_counter()
+        od.solve(sub, H, tol=w.tol)
+        t_used += time.perf_counter() - t0
+        n_done += len(take)
+        solves += len(take) * w.n_poles
+        k = min(2 * k, 16)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": solves / t_used, "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n_done} nodes x {w.n_poles} poles of {w.name} (FP64 COCG, tol {w.tol:g}), "
+                      f"{t_used:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from synthetic import make_workload
+    from oracle import _native
+    _native.build()
+    w = make_workload(args.workload)
+    budget = 20.0
+    # each step: a bounded batch of nodes (all poles) of the same workload
+    from oracle import density as od
+    H = od.build(w)
+    per_step_nodes = 1
+    t = time.perf_counter()
+    od.solve(w.subset(np.arange(1)), H, tol=w.tol)
+    one = time.perf_counter() - t
+    per_step_nodes = max(1, int(budget / max(args.steps + args.warmup, 1) / max(one, 1e-3)))
+    cursor = 1
+    for _ in range(args.warmup):
+        od.solve(w.subset(np.arange(cursor, cursor + per_step_nodes) % len(w.nodes)), H, tol=w.tol)
+        cursor += per_step_nodes
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        od.solve(w.subset(np.arange(cursor, cursor + per_step_nodes) % len(w.nodes)), H, tol=w.tol)
+        cursor += per_step_nodes
+    el = time.perf_counter() - t0
+    solves = args.steps * per_step_nodes * w.n_poles
+    val = solves / el
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "nodes_per_step": per_step_nodes, "poles": w.n_poles},
+           "cpu_baseline": {"value": val, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                            "sample": f"{per_step_nodes} nodes x {w.n_poles} poles per step of {w.name}"},
+           "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, dist = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    from synthetic import make_workload
+    from paper_1907_02604_gb300 import Hamiltonian, SolverOptions, density, make_poles
+    from paper_1907_02604_gb300 import _lib
+
+    w = make_workload(args.workload)
+    prec = args.precision or w.precision
+    n_nodes = len(w.nodes)
+    bs = min(args.nodes_per_step, n_nodes)
+    n_batches = max(1, n_nodes // bs)
+    opts = SolverOptions(tol=w.tol, maxit=w.maxit, precision=prec, block=args.block,
+                         ctas_per_sm=args.ctas_per_sm)
+    stream = torch.cuda.current_stream()
+
+    def batch(i):
+        b = (i * world + rank) % n_batches
+        sl = slice(b * bs, (b + 1) * bs)
+        return w.nodes[sl], w.halfwidth[sl]
+
+    # ---- device-resident inputs: Hamiltonian built before timing ----------
+    ham = Hamiltonian.from_workload(w)
+    lo, hi = ham.spectral_bounds()
+    rho_buf = torch.empty(bs, dtype=torch.float64, device="cuda")
+
+    def step(i, stats_acc):
+        nd, hw = batch(i)
+        z, wt = make_poles(w.kT, w.mu, lo, hi, w.n_poles)
+        _, _, st = density(ham, z, wt, nd, hw, opts, energy=True, out=rho_buf, stream=stream)
+        stats_acc.append(st)
+
+    warm = []
+    for i in range(args.warmup):
+        step(i, warm)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    stats = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i, stats)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    el_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([el_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+        dist.barrier()
+    solves_rank = sum(s["n_systems"] for s in stats)
+    total_solves = solves_rank * world
+    value = total_solves / (el_ms / 1e3)
+    kernel_ms = sum(s["kernel_ms"] for s in stats)
+    point_iters = sum(s["total_point_iters"] for s in stats)
+    conv = sum(s["n_converged"] for s in stats)
+    B = BYTES_PER_POINT_ITER[prec]
+    achieved = point_iters * B / (kernel_ms / 1e3) / 1e9
+    peak, peak_kind = read_peaks()
+
+    # ---- end to end through the C ABI from host buffers -------------------
+    e2e = None
+    if not args.no_e2e:
+        h2d = d2h = 0
+
+        def e2e_step(i):
+            nonlocal h2d, d2h
+            nd, hw = batch(i)
+            hm = Hamiltonian.from_workload(w, stream=stream)
+            l2, h2 = hm.spectral_bounds(stream=stream)
+            z, wt = make_poles(w.kT, w.mu, l2, h2, w.n_poles)
+            rho, e, st = density(hm, z, wt, nd, hw, opts, energy=True, stream=stream)
+            rho_h, e_h = rho.cpu(), e.cpu()
+            hm.close()
+            h2d = (w.v_ext.nbytes + w.atoms.nbytes + w.depth.nbytes + w.sigma.nbytes
+                   + nd.nbytes + hw.nbytes + 32 * w.n_poles)
+            d2h = rho_h.numel() * 8 + e_h.numel() * 8 + st["n_systems"] * 20
+            return st["n_systems"]
+
+        for i in range(min(args.warmup, 3)):
+            e2e_step(i)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        n_e2e = sum(e2e_step(args.warmup + i) for i in range(args.steps))
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": n_e2e * world / el, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = cpu_oracle_sample(w)
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": el_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64" if prec == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "nodes_per_step": bs, "poles": w.n_poles,
+                   "region": "33^3", "grid": list(w.shape), "atoms": len(w.atoms),
+                   "fd_order": w.fd_order, "precision": prec, "tol": w.tol,
+                   "l2": "no flush: per-step working set (Krylov slots) > 129 MB L2",
+                   "parallelism": f"nodes sharded over {world} GPU(s), no collective"},
+        "nodes_per_s": value / w.n_poles,
+        "converged": f"{conv}/{solves_rank}",
+        "iters_mean": float(np.mean([s["iters_mean"] for s in stats])),
+        "point_iters_per_s": point_iters * world / (el_ms / 1e3),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_cocg<MixedMode>" if prec == "mixed" else "k_cocg<FP64Mode>",
+                     "bytes_per_point_iter": B, "peak_kind": peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
