@@ -97,7 +97,8 @@ md_status check_device() {
 void free_ham(Ham& H) {
     void* ptrs[] = {H.V, H.V32, H.atom_xyz, H.atom_depth, H.atom_sigma, H.proj_i0, H.proj_len,
                     H.proj_d, H.proj_g, H.proj_d32, H.proj_g32, H.proj_C, H.proj_absum,
-                    H.proj_C32, H.proj_rows, H.pl_ptr, H.pl_atom, H.scratch};
+                    H.proj_C32, H.proj_rows, H.pl_ptr, H.pl_atom, H.pl_val32, H.pl_val64,
+                    H.scratch};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -169,8 +170,8 @@ md_solver_opts normalise_opts(const md_solver_opts* o) {
     md_solver_opts r;
     std::memset(&r, 0, sizeof(r));
     if (o) r = *o;
-    if (r.reliable_every <= 0) r.reliable_every = 200;
-    if (!(r.reliable_delta > 0.0)) r.reliable_delta = 1e-2;
+    if (r.reliable_every <= 0) r.reliable_every = 1000;
+    if (!(r.reliable_delta > 0.0)) r.reliable_delta = 1e-3;
     return r;
 }
 
@@ -291,6 +292,8 @@ md_status run_solver(Ham& H, const md_poles* poles, const Regions& R, const md_s
     P.proj_rows = H.proj_rows;
     P.pl_ptr = H.pl_ptr;
     P.pl_atom = H.pl_atom;
+    P.pl_val32 = H.pl_val32;
+    P.pl_val64 = H.pl_val64;
     P.e_s = H.e_s;
     P.e_p = H.e_p;
     P.n_sys = (int)n_sys;

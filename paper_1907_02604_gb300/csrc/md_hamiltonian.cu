@@ -235,12 +235,15 @@ __device__ __forceinline__ int window_slot(int i, int i0, int len, int n, int pe
 }
 
 // Per grid point: atoms whose projector support contains the point (the
-// row-interval test above), ascending atom id.
+// row-interval test above), ascending atom id.  The fill pass also stores
+// the four normalised projector values at the point (FP64 and FP32).
 template <bool kFill>
 __global__ void k_proj_lists(GridGeo g, CellArgs cl, const int* __restrict__ i0,
                              const int* __restrict__ len, const unsigned char* __restrict__ rows,
-                             long long N, long long* __restrict__ count_or_ptr,
-                             int* __restrict__ out_atoms, int* __restrict__ overflow) {
+                             const double* __restrict__ dtab, const double* __restrict__ gtab,
+                             const double* __restrict__ C, long long N, int* __restrict__ count_or_ptr,
+                             int* __restrict__ out_atoms, double2* __restrict__ val64,
+                             float4* __restrict__ val32, int* __restrict__ overflow) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
         const int ix = (int)(i % g.n[0]);
@@ -273,7 +276,24 @@ __global__ void k_proj_lists(GridGeo g, CellArgs cl, const int* __restrict__ i0,
                 ids[y + 1] = v;
             }
             const long long base = count_or_ptr[i];
-            for (int x = 0; x < m; ++x) out_atoms[base + x] = ids[x];
+            const int pi[3] = {ix, iy, iz};
+            for (int x = 0; x < m; ++x) {
+                const int a = ids[x];
+                out_atoms[base + x] = a;
+                int uu[3];
+                for (int d = 0; d < 3; ++d)
+                    uu[d] = window_slot(pi[d], i0[3 * a + d], len[3 * a + d], g.n[d], g.periodic[d]);
+                const double* dt = dtab + 3 * (long long)a * kMaxProjWin;
+                const double* gt = gtab + 3 * (long long)a * kMaxProjWin;
+                const double gg = gt[uu[0]] * gt[kMaxProjWin + uu[1]] * gt[2 * kMaxProjWin + uu[2]];
+                const double p0 = C[4 * a + 0] * gg;
+                const double p1 = C[4 * a + 1] * dt[uu[0]] * gg;
+                const double p2 = C[4 * a + 2] * dt[kMaxProjWin + uu[1]] * gg;
+                const double p3 = C[4 * a + 3] * dt[2 * kMaxProjWin + uu[2]] * gg;
+                val64[2 * (base + x) + 0] = make_double2(p0, p1);
+                val64[2 * (base + x) + 1] = make_double2(p2, p3);
+                val32[base + x] = make_float4((float)p0, (float)p1, (float)p2, (float)p3);
+            }
         }
     }
 }
@@ -281,7 +301,7 @@ __global__ void k_proj_lists(GridGeo g, CellArgs cl, const int* __restrict__ i0,
 // Per grid point Gershgorin disc; per block min of (diag - radius) and
 // max of (diag + radius).
 __global__ void k_gershgorin(GridGeo g, const double* __restrict__ V, double diag0, double rad0,
-                             long long N, int nonlocal, const long long* __restrict__ pl_ptr,
+                             long long N, int nonlocal, const int* __restrict__ pl_ptr,
                              const int* __restrict__ pl_atom, const int* __restrict__ i0,
                              const int* __restrict__ len, const double* __restrict__ dtab,
                              const double* __restrict__ gtab, const double* __restrict__ C,
@@ -297,7 +317,7 @@ __global__ void k_gershgorin(GridGeo g, const double* __restrict__ V, double dia
             const int iy = (int)((i / g.n[0]) % g.n[1]);
             const int iz = (int)(i / ((long long)g.n[0] * g.n[1]));
             const int pi[3] = {ix, iy, iz};
-            for (long long e = pl_ptr[i]; e < pl_ptr[i + 1]; ++e) {
+            for (int e = pl_ptr[i]; e < pl_ptr[i + 1]; ++e) {
                 const int a = pl_atom[e];
                 int uu[3];
                 for (int d = 0; d < 3; ++d)
@@ -465,7 +485,7 @@ md_status build_hamiltonian_device(Ham& H, const md_atoms* atoms, const md_pot_p
     int* d_cids = nullptr;
     double* d_vext = nullptr;
     int* d_overflow = nullptr;
-    long long* d_count = nullptr;
+    int* d_count = nullptr;
     double max_sigma = 0.0;
     GridGeo g = geo_of(H);
     const int threads = 256;
@@ -546,16 +566,17 @@ md_status build_hamiltonian_device(Ham& H, const md_atoms* atoms, const md_pot_p
             ca.cell[d] = cellp[d];
         }
         ca.start = d_cstart;
-        MD_CUDA_TRY(cudaMalloc(&d_count, (N + 1) * sizeof(long long)));
+        MD_CUDA_TRY(cudaMalloc(&d_count, (N + 1) * sizeof(int)));
         MD_CUDA_TRY(cudaMalloc(&d_overflow, sizeof(int)));
         MD_CUDA_TRY(cudaMemsetAsync(d_overflow, 0, sizeof(int), stream));
         k_proj_lists<false><<<blocks, threads, 0, stream>>>(g, ca, H.proj_i0, H.proj_len, H.proj_rows,
-                                                            N, d_count, nullptr, d_overflow);
+                                                            H.proj_d, H.proj_g, H.proj_C, N, d_count,
+                                                            nullptr, nullptr, nullptr, d_overflow);
         MD_CUDA_TRY(cudaGetLastError());
         {
-            std::vector<long long> cnt(N + 1, 0);
+            std::vector<int> cnt(N + 1, 0);
             int ovf = 0;
-            MD_CUDA_TRY(cudaMemcpyAsync(cnt.data(), d_count, N * sizeof(long long), cudaMemcpyDeviceToHost, stream));
+            MD_CUDA_TRY(cudaMemcpyAsync(cnt.data(), d_count, N * sizeof(int), cudaMemcpyDeviceToHost, stream));
             MD_CUDA_TRY(cudaMemcpyAsync(&ovf, d_overflow, sizeof(int), cudaMemcpyDeviceToHost, stream));
             MD_CUDA_TRY(cudaStreamSynchronize(stream));
             if (ovf) {
@@ -565,17 +586,24 @@ md_status build_hamiltonian_device(Ham& H, const md_atoms* atoms, const md_pot_p
             long long run = 0;
             for (long long i = 0; i < N; ++i) {
                 const long long c = cnt[i];
-                cnt[i] = run;
+                if (run > 2147483647LL - 16) {
+                    st = set_error(MD_ERR_INVALID, "md_build_hamiltonian: too many projector entries (2^31)");
+                    goto fail;
+                }
+                cnt[i] = (int)run;
                 run += c;
             }
-            cnt[N] = run;
+            cnt[N] = (int)run;
             H.pl_nnz = run;
-            MD_CUDA_TRY(cudaMalloc(&H.pl_ptr, (N + 1) * sizeof(long long)));
+            MD_CUDA_TRY(cudaMalloc(&H.pl_ptr, (N + 1) * sizeof(int)));
             MD_CUDA_TRY(cudaMalloc(&H.pl_atom, std::max<long long>(run, 1) * sizeof(int)));
-            MD_CUDA_TRY(cudaMemcpy(H.pl_ptr, cnt.data(), (N + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+            MD_CUDA_TRY(cudaMalloc(&H.pl_val32, std::max<long long>(run, 1) * sizeof(float4)));
+            MD_CUDA_TRY(cudaMalloc(&H.pl_val64, std::max<long long>(run, 1) * 2 * sizeof(double2)));
+            MD_CUDA_TRY(cudaMemcpy(H.pl_ptr, cnt.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice));
         }
         k_proj_lists<true><<<blocks, threads, 0, stream>>>(g, ca, H.proj_i0, H.proj_len, H.proj_rows,
-                                                           N, H.pl_ptr, H.pl_atom, d_overflow);
+                                                           H.proj_d, H.proj_g, H.proj_C, N, H.pl_ptr,
+                                                           H.pl_atom, H.pl_val64, H.pl_val32, d_overflow);
         MD_CUDA_TRY(cudaGetLastError());
     }
     {

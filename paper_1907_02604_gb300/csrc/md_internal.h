@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <string>
 
+#include <vector_types.h>
+
 #include "../../include/macrodft.h"
 
 namespace md {
@@ -58,8 +60,10 @@ struct Ham {
     double* proj_absum = nullptr;     // [n_atoms][4] sum_i |p(i)| (Gershgorin radii)
     float* proj_C32 = nullptr;
     unsigned char* proj_rows = nullptr; // [n_atoms][W][W][2]: in-sphere u range of row (v, w)
-    long long* pl_ptr = nullptr;      // [N+1] per-point projector-atom lists
+    int* pl_ptr = nullptr;            // [N+1] per-point projector-atom lists
     int* pl_atom = nullptr;           // [nnz] atom ids, ascending per point
+    float4* pl_val32 = nullptr;       // [nnz] (p_s, p_x, p_y, p_z) at the point, FP32
+    double2* pl_val64 = nullptr;      // [nnz][2] the same in FP64
     long long pl_nnz = 0;
 
     bool bounds_valid = false;

@@ -4,8 +4,8 @@
 // from a global work counter when it finishes (persistent scheduling over a
 // cost-sorted list: largest regions and poles nearest the real axis
 // first).  The Krylov vectors of the system live in a per-CTA slot of
-// device scratch memory; the Hamiltonian (V, projector tables) is shared by
-// all systems and stays in L2.
+// device scratch memory; the Hamiltonian (V, projector tables and
+// per-point projector values) is shared by all systems and stays in L2.
 //
 // Per COCG iteration (van der Vorst & Melissen 1990; bilinear u^T v, since
 // H_R - z is complex symmetric):
@@ -18,15 +18,21 @@
 // Precision modes:
 //   FP64   every vector, scalar and product in double.
 //   MIXED  p, r, Ap, the stencil, V and the projector values in float;
-//          the solution is x_hi (double) + dx (float, reset at each
-//          flush); each product/partial sum in a thread's run of points is
-//          float, everything from the per-thread partial upward (warp and
-//          block reductions, alpha, beta, norms) is double.  A reliable
-//          update (van der Vorst & Ye 2000) recomputes the residual
-//          r = e_j - (H_R - z) x_hi in double every `reliable_every`
-//          iterations, whenever ||r|| fell by `reliable_delta` since the
-//          last one, and before convergence is declared: the returned
-//          solution always meets tol on its FP64 residual.
+//          the solution is x_hi (double) + dx (float, flushed into x_hi at
+//          each residual refresh).  Products and each thread's partial sum
+//          over its own points (at most a few dozen terms) are float;
+//          everything from the per-thread partial upward (warp and block
+//          reductions, alpha, beta, norms) is double.  A reliable update
+//          (van der Vorst & Ye, SIAM J. Sci. Comput. 22, 2000) recomputes
+//          the residual r = e_j - (H_R - z) x_hi in double every
+//          `reliable_every` iterations, whenever ||r|| fell by
+//          `reliable_delta` since the last one, and before convergence is
+//          declared, so the returned solution meets tol on its FP64
+//          residual.
+//
+// Index arithmetic: each thread walks region points i = tid, tid + T, ...
+// (coalesced); (a, b, c) come from i by multiply-shift division by the
+// invariant row and plane sizes (Granlund & Montgomery, PLDI 1994).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -39,54 +45,74 @@ namespace md {
 
 namespace {
 
-struct RegionGeo {
-    int m[3];     // region points per axis
-    int lo[3];    // unwrapped global coordinate of local 0 (ring axes: 0)
-    int ring[3];  // axis is a whole periodic ring
-    int n;        // total points
+constexpr int kLocal = kMaxLocalProjAtoms;
+constexpr int kMapMax = 4096;   // direct global->local atom map when n_atoms <= this
+
+struct FastDiv {
+    uint32_t m;
+    uint32_t l;
+};
+
+__device__ __forceinline__ FastDiv make_fastdiv(uint32_t d) {
+    uint32_t l = 0;
+    while ((1u << l) < d) ++l;
+    const uint64_t m = ((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1;
+    return FastDiv{(uint32_t)m, l};
+}
+
+// n / d for 0 <= n < 2^31
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, FastDiv f) { return (__umulhi(n, f.m) + n) >> f.l; }
+
+struct Geo {
+    int m[3];
+    int lo[3];
+    int ring[3];
+    int any_ring;
+    int n;
+    int plane;
     int src;
+    FastDiv div_row, div_plane;
 };
 
 template <class R>
-struct Tables;
-
+struct Tab;
 template <>
-struct Tables<double> {
+struct Tab<double> {
     __device__ static const double* d(const SolveParams& P) { return P.proj_d; }
     __device__ static const double* g(const SolveParams& P) { return P.proj_g; }
     __device__ static const double* C(const SolveParams& P) { return P.proj_C; }
-    __device__ static double V(const SolveParams& P, long long gi) { return P.V[gi]; }
+    __device__ static double V(const SolveParams& P, long long gi) { return __ldg(P.V + gi); }
 };
 template <>
-struct Tables<float> {
+struct Tab<float> {
     __device__ static const float* d(const SolveParams& P) { return P.proj_d32; }
     __device__ static const float* g(const SolveParams& P) { return P.proj_g32; }
     __device__ static const float* C(const SolveParams& P) { return P.proj_C32; }
-    __device__ static float V(const SolveParams& P, long long gi) { return P.V32[gi]; }
+    __device__ static float V(const SolveParams& P, long long gi) { return __ldg(P.V32 + gi); }
 };
 
 struct Shared {
-    // nonlocal: local atom list (ascending id), window offsets in region coordinates
-    int n_local;
-    int la_id[kMaxLocalProjAtoms];
-    short la_off[kMaxLocalProjAtoms][3];
-    double2 c[kMaxLocalProjAtoms][4];     // projector coefficients of the current vector
     double red[32][4];
     double bcast[4];
+    double coefD[3][kMaxQ];
+    float coefF[3][kMaxQ];
     int sys;
     int flag;
+    int n_local;
+    int la_id[kLocal];
+    short la_off[kLocal][3];
+    double2 c[kLocal][4];   // E_l dV C_l sum_i f_l(i) v(i), double
+    float2 cf[kLocal][4];   // the same rounded to float
+    short map[kMapMax];     // global atom id -> local slot, -1 if absent
 };
 
-__device__ __forceinline__ long long global_index(const SolveParams& P, const RegionGeo& G, int a, int b,
-                                                  int c) {
-    int gx = G.lo[0] + a, gy = G.lo[1] + b, gz = G.lo[2] + c;
-    gx = (gx % P.n[0] + P.n[0]) % P.n[0];
-    gy = (gy % P.n[1] + P.n[1]) % P.n[1];
-    gz = (gz % P.n[2] + P.n[2]) % P.n[2];
-    return gx + (long long)P.n[0] * (gy + (long long)P.n[1] * gz);
-}
+template <class R>
+__device__ __forceinline__ const R* coef_of(const Shared& S);
+template <>
+__device__ __forceinline__ const double* coef_of<double>(const Shared& S) { return &S.coefD[0][0]; }
+template <>
+__device__ __forceinline__ const float* coef_of<float>(const Shared& S) { return &S.coefF[0][0]; }
 
-// Block-wide sum of K doubles (K <= 4); every thread gets the result.
 template <int K>
 __device__ __forceinline__ void block_sum(Shared& S, double (&v)[K]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -108,10 +134,15 @@ __device__ __forceinline__ void block_sum(Shared& S, double (&v)[K]) {
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = S.bcast[k];
-    __syncthreads();
 }
 
-// Region slot of window index u of an atom window starting at region offset off.
+__device__ __forceinline__ int wrap_once(int g, int n) {
+    g += (g < 0) ? n : 0;
+    g -= (g >= n) ? n : 0;
+    return g;
+}
+
+// Region slot of window index u for an atom window starting at region offset off.
 __device__ __forceinline__ int region_slot(int off, int u, int n, int m) {
     int a = off + u;
     if (a >= n) a -= n;
@@ -119,7 +150,7 @@ __device__ __forceinline__ int region_slot(int off, int u, int n, int m) {
 }
 
 // Local atoms whose projector window meets the region; ascending atom id.
-__device__ void collect_local_atoms(const SolveParams& P, const RegionGeo& G, Shared& S) {
+__device__ void collect_local_atoms(const SolveParams& P, const Geo& G, Shared& S) {
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         int count = 0;
@@ -135,9 +166,7 @@ __device__ void collect_local_atoms(const SolveParams& P, const RegionGeo& G, Sh
                     if (P.periodic[d]) {
                         o %= P.n[d];
                         if (o < 0) o += P.n[d];
-                        // window covers region slots o..o+len-1 (mod n); meets [0, m)?
-                        const bool meet = (o < G.m[d]) || (o + len - 1 >= P.n[d]);
-                        hit = hit && meet;
+                        hit = hit && ((o < G.m[d]) || (o + len - 1 >= P.n[d]));
                     } else {
                         hit = hit && (o < G.m[d]) && (o + len - 1 >= 0);
                     }
@@ -147,77 +176,32 @@ __device__ void collect_local_atoms(const SolveParams& P, const RegionGeo& G, Sh
             const unsigned mask = __ballot_sync(0xffffffffu, hit);
             if (hit) {
                 const int slot = count + __popc(mask & ((1u << lane) - 1u));
-                if (slot < kMaxLocalProjAtoms) {
+                if (slot < kLocal) {
                     S.la_id[slot] = (int)a;
                     S.la_off[slot][0] = off[0];
                     S.la_off[slot][1] = off[1];
                     S.la_off[slot][2] = off[2];
+                    if (P.n_atoms <= kMapMax) S.map[a] = (short)slot;
                 }
             }
             count += __popc(mask);
         }
         if (lane == 0) {
-            S.n_local = count < kMaxLocalProjAtoms ? count : kMaxLocalProjAtoms;
-            if (count > kMaxLocalProjAtoms) S.flag = 1;
+            S.n_local = count < kLocal ? count : kLocal;
+            if (count > kLocal) S.flag = 1;
         }
     }
     __syncthreads();
 }
 
-// c_al = sum_{i in region} p_al(i) v(i) for every local atom (warp per atom).
-template <class R, class C>
-__device__ void nonlocal_coeffs(const SolveParams& P, const RegionGeo& G, Shared& S, const C* __restrict__ v) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const R* dt = Tables<R>::d(P);
-    const R* gt = Tables<R>::g(P);
-    const R* Ct = Tables<R>::C(P);
-    for (int k = warp; k < S.n_local; k += nw) {
-        const int a = S.la_id[k];
-        const int lx = P.proj_len[3 * a], ly = P.proj_len[3 * a + 1], lz = P.proj_len[3 * a + 2];
-        const R* dx = dt + (3LL * a + 0) * kMaxProjWin;
-        const R* dy = dt + (3LL * a + 1) * kMaxProjWin;
-        const R* dz = dt + (3LL * a + 2) * kMaxProjWin;
-        const R* gx = gt + (3LL * a + 0) * kMaxProjWin;
-        const R* gy = gt + (3LL * a + 1) * kMaxProjWin;
-        const R* gz = gt + (3LL * a + 2) * kMaxProjWin;
-        R acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int row = lane; row < ly * lz; row += 32) {
-            const int vv = row % ly, ww = row / ly;
-            const int b = region_slot(S.la_off[k][1], vv, P.n[1], G.m[1]);
-            const int c = region_slot(S.la_off[k][2], ww, P.n[2], G.m[2]);
-            if (b < 0 || c < 0) continue;
-            const unsigned char* rw = P.proj_rows + 2 * (((long long)a * kMaxProjWin + ww) * kMaxProjWin + vv);
-            const int u0 = rw[0], u1 = rw[1];
-            const R gyz = gy[vv] * gz[ww];
-            for (int u = u0; u <= u1 && u < lx; ++u) {
-                const int aa = region_slot(S.la_off[k][0], u, P.n[0], G.m[0]);
-                if (aa < 0) continue;
-                const C pv = v[aa + G.m[0] * (b + G.m[1] * c)];
-                const R gg = gx[u] * gyz;
-                const R f0 = gg, f1 = dx[u] * gg, f2 = dy[vv] * gg, f3 = dz[ww] * gg;
-                acc[0] += f0 * pv.x; acc[1] += f0 * pv.y;
-                acc[2] += f1 * pv.x; acc[3] += f1 * pv.y;
-                acc[4] += f2 * pv.x; acc[5] += f2 * pv.y;
-                acc[6] += f3 * pv.x; acc[7] += f3 * pv.y;
-            }
-        }
-        double s[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) s[t] = warp_sum((double)acc[t]);
-        if (lane == 0) {
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const double Cl = (double)Ct[4LL * a + l];
-                const double E = (l == 0 ? P.e_s : P.e_p) * P.dV;
-                // store E dV C c so the apply step only multiplies by the shape
-                S.c[k][l] = make_double2(E * Cl * s[2 * l], E * Cl * s[2 * l + 1]);
-            }
-        }
-    }
+__device__ void release_local_atoms(const SolveParams& P, Shared& S) {
+    if (P.n_atoms <= kMapMax)
+        for (int k = threadIdx.x; k < S.n_local; k += blockDim.x) S.map[S.la_id[k]] = -1;
     __syncthreads();
 }
 
-__device__ __forceinline__ int find_local(const Shared& S, int atom) {
+__device__ __forceinline__ int local_slot(const SolveParams& P, const Shared& S, int atom) {
+    if (P.n_atoms <= kMapMax) return S.map[atom];
     int lo = 0, hi = S.n_local - 1;
     while (lo <= hi) {
         const int mid = (lo + hi) >> 1;
@@ -229,91 +213,188 @@ __device__ __forceinline__ int find_local(const Shared& S, int atom) {
     return -1;
 }
 
-// y = (H_R - z) v at local point (a, b, c), linear index i, in real type R.
-template <class R, class C, class CIn>
-__device__ __forceinline__ C apply_point(const SolveParams& P, const RegionGeo& G, const Shared& S,
-                                         const CIn* __restrict__ v, int i, int a, int b, int c, C z) {
-    const long long gi = global_index(P, G, a, b, c);
-    const CIn vi = v[i];
-    const R dg = (R)P.diag + Tables<R>::V(P, gi);
-    C y = cmake<C>((dg - z.x) * (R)vi.x + z.y * (R)vi.y, (dg - z.x) * (R)vi.y - z.y * (R)vi.x);
-    const int pos[3] = {a, b, c};
-    const int stride[3] = {1, G.m[0], G.m[0] * G.m[1]};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int md = G.m[d];
-        for (int o = 1; o <= P.q; ++o) {
-            const R w = (R)P.coef[d][o - 1];
-            R sx = 0, sy = 0;
-            int tp = pos[d] + o, tm = pos[d] - o;
-            if (G.ring[d]) {
-                tp %= md;
-                tm = ((tm % md) + md) % md;
-                const CIn up = v[i + (tp - pos[d]) * stride[d]];
-                const CIn dn = v[i + (tm - pos[d]) * stride[d]];
-                sx = (R)up.x + (R)dn.x;
-                sy = (R)up.y + (R)dn.y;
-            } else {
-                if (tp < md) {
-                    const CIn up = v[i + o * stride[d]];
-                    sx += (R)up.x;
-                    sy += (R)up.y;
-                }
-                if (tm >= 0) {
-                    const CIn dn = v[i - o * stride[d]];
-                    sx += (R)dn.x;
-                    sy += (R)dn.y;
-                }
+// c_al = E_l dV sum_{i in region} p_al(i) v(i) (warp per atom, two rows per step).
+template <class R, class C>
+__device__ void nonlocal_coeffs(const SolveParams& P, const Geo& G, Shared& S, const C* __restrict__ v) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int half = lane >> 4, hl = lane & 15;
+    const R* dt = Tab<R>::d(P);
+    const R* gt = Tab<R>::g(P);
+    for (int k = warp; k < S.n_local; k += nw) {
+        const int a = S.la_id[k];
+        const int lx = __ldg(P.proj_len + 3 * a), ly = __ldg(P.proj_len + 3 * a + 1),
+                  lz = __ldg(P.proj_len + 3 * a + 2);
+        const R* dx = dt + (3LL * a + 0) * kMaxProjWin;
+        const R* dy = dt + (3LL * a + 1) * kMaxProjWin;
+        const R* dz = dt + (3LL * a + 2) * kMaxProjWin;
+        const R* gx = gt + (3LL * a + 0) * kMaxProjWin;
+        const R* gy = gt + (3LL * a + 1) * kMaxProjWin;
+        const R* gz = gt + (3LL * a + 2) * kMaxProjWin;
+        const unsigned char* rows = P.proj_rows + 2LL * a * kMaxProjWin * kMaxProjWin;
+        R acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const int nrows = ly * lz;
+        for (int r0 = 0; r0 < nrows; r0 += 2) {
+            const int row = r0 + half;
+            if (row >= nrows) continue;
+            const int ww = row / ly, vv = row - ww * ly;
+            const int b = region_slot(S.la_off[k][1], vv, P.n[1], G.m[1]);
+            const int c = region_slot(S.la_off[k][2], ww, P.n[2], G.m[2]);
+            if (b < 0 || c < 0) continue;
+            const unsigned char* rw = rows + 2 * (ww * kMaxProjWin + vv);
+            const int u0 = rw[0], u1 = min((int)rw[1], lx - 1);
+            const R gyz = __ldg(gy + vv) * __ldg(gz + ww);
+            const R ey = __ldg(dy + vv), ez = __ldg(dz + ww);
+            const int base_i = G.m[0] * (b + G.m[1] * c);
+            for (int u = u0 + hl; u <= u1; u += 16) {
+                const int aa = region_slot(S.la_off[k][0], u, P.n[0], G.m[0]);
+                if (aa < 0) continue;
+                const C pv = v[base_i + aa];
+                const R gg = __ldg(gx + u) * gyz;
+                const R f1 = __ldg(dx + u) * gg, f2 = ey * gg, f3 = ez * gg;
+                acc[0] += gg * (R)pv.x; acc[1] += gg * (R)pv.y;
+                acc[2] += f1 * (R)pv.x; acc[3] += f1 * (R)pv.y;
+                acc[4] += f2 * (R)pv.x; acc[5] += f2 * (R)pv.y;
+                acc[6] += f3 * (R)pv.x; acc[7] += f3 * (R)pv.y;
             }
-            y.x += w * sx;
-            y.y += w * sy;
+        }
+        double s[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) s[t] = warp_sum((double)acc[t]);
+        if (lane < 4) {
+            const double Cl = (double)__ldg(P.proj_C + 4LL * a + lane);
+            const double E = (lane == 0 ? P.e_s : P.e_p) * P.dV * Cl;
+            double sr = s[0], si = s[1];
+            if (lane == 1) { sr = s[2]; si = s[3]; }
+            if (lane == 2) { sr = s[4]; si = s[5]; }
+            if (lane == 3) { sr = s[6]; si = s[7]; }
+            S.c[k][lane] = make_double2(E * sr, E * si);
+            S.cf[k][lane] = make_float2((float)(E * sr), (float)(E * si));
+        }
+    }
+    __syncthreads();
+}
+
+template <class R>
+struct PVal;
+template <>
+struct PVal<float> {
+    __device__ static void get(const SolveParams& P, int e, float (&f)[4]) {
+        const float4 v = __ldg(P.pl_val32 + e);
+        f[0] = v.x; f[1] = v.y; f[2] = v.z; f[3] = v.w;
+    }
+    __device__ static float2 c(const Shared& S, int k, int l) { return S.cf[k][l]; }
+};
+template <>
+struct PVal<double> {
+    __device__ static void get(const SolveParams& P, int e, double (&f)[4]) {
+        const double2 a = __ldg(P.pl_val64 + 2 * e), b = __ldg(P.pl_val64 + 2 * e + 1);
+        f[0] = a.x; f[1] = a.y; f[2] = b.x; f[3] = b.y;
+    }
+    __device__ static double2 c(const Shared& S, int k, int l) { return S.c[k][l]; }
+};
+
+// y = (H_R - z) v at region point i (Q = stencil half-width), arithmetic in R.
+template <class R, class C, int Q, class CIn>
+__device__ __forceinline__ C matvec_point(const SolveParams& P, const Geo& G, const Shared& S,
+                                          const CIn* __restrict__ v, int i, R zr, R zi, R diag) {
+    const int c = (int)fdiv((uint32_t)i, G.div_plane);
+    const int rem = i - c * G.plane;
+    const int b = (int)fdiv((uint32_t)rem, G.div_row);
+    const int a = rem - b * G.m[0];
+    const int gx = wrap_once(G.lo[0] + a, P.n[0]);
+    const int gy = wrap_once(G.lo[1] + b, P.n[1]);
+    const int gz = wrap_once(G.lo[2] + c, P.n[2]);
+    const long long gi = gx + (long long)P.n[0] * (gy + (long long)P.n[1] * gz);
+    const CIn vi = v[i];
+    const R dg = diag + Tab<R>::V(P, gi) - zr;
+    R yx = dg * (R)vi.x + zi * (R)vi.y;
+    R yy = dg * (R)vi.y - zi * (R)vi.x;
+    const R* cf = coef_of<R>(S);
+    const int pos[3] = {a, b, c};
+    const int stride[3] = {1, G.m[0], G.plane};
+    if (!G.any_ring) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+#pragma unroll
+            for (int o = 1; o <= Q; ++o) {
+                const R w = cf[d * kMaxQ + (o - 1)];
+                R sx = 0, sy = 0;
+                if (pos[d] + o < G.m[d]) {
+                    const CIn t = v[i + o * stride[d]];
+                    sx += (R)t.x;
+                    sy += (R)t.y;
+                }
+                if (pos[d] - o >= 0) {
+                    const CIn t = v[i - o * stride[d]];
+                    sx += (R)t.x;
+                    sy += (R)t.y;
+                }
+                yx += w * sx;
+                yy += w * sy;
+            }
+        }
+    } else {
+        for (int d = 0; d < 3; ++d) {
+            const int md = G.m[d];
+            for (int o = 1; o <= Q; ++o) {
+                const R w = cf[d * kMaxQ + (o - 1)];
+                R sx = 0, sy = 0;
+                if (G.ring[d]) {
+                    const int tp = (pos[d] + o) % md;
+                    const int tm = ((pos[d] - o) % md + md) % md;
+                    const CIn up = v[i + (tp - pos[d]) * stride[d]];
+                    const CIn dn = v[i + (tm - pos[d]) * stride[d]];
+                    sx = (R)up.x + (R)dn.x;
+                    sy = (R)up.y + (R)dn.y;
+                } else {
+                    if (pos[d] + o < md) {
+                        const CIn t = v[i + o * stride[d]];
+                        sx += (R)t.x;
+                        sy += (R)t.y;
+                    }
+                    if (pos[d] - o >= 0) {
+                        const CIn t = v[i - o * stride[d]];
+                        sx += (R)t.x;
+                        sy += (R)t.y;
+                    }
+                }
+                yx += w * sx;
+                yy += w * sy;
+            }
         }
     }
     if (P.nonlocal) {
-        const R* dt = Tables<R>::d(P);
-        const R* gt = Tables<R>::g(P);
-        const R* Ct = Tables<R>::C(P);
-        const int gx = (int)(gi % P.n[0]);
-        const int gy = (int)((gi / P.n[0]) % P.n[1]);
-        const int gz = (int)(gi / ((long long)P.n[0] * P.n[1]));
-        for (long long e = P.pl_ptr[gi]; e < P.pl_ptr[gi + 1]; ++e) {
-            const int at = P.pl_atom[e];
-            const int k = find_local(S, at);
+        const int e0 = __ldg(P.pl_ptr + gi), e1 = __ldg(P.pl_ptr + gi + 1);
+        for (int e = e0; e < e1; ++e) {
+            const int k = local_slot(P, S, __ldg(P.pl_atom + e));
             if (k < 0) continue;
-            int uu[3];
-            const int gp[3] = {gx, gy, gz};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                int u = gp[d] - P.proj_i0[3 * at + d];
-                if (P.periodic[d]) {
-                    u %= P.n[d];
-                    if (u < 0) u += P.n[d];
-                }
-                uu[d] = u;
-            }
-            const R* ds = dt + 3LL * at * kMaxProjWin;
-            const R* gs = gt + 3LL * at * kMaxProjWin;
-            const R gg = gs[uu[0]] * gs[kMaxProjWin + uu[1]] * gs[2 * kMaxProjWin + uu[2]];
-            const R f[4] = {gg, ds[uu[0]] * gg, ds[kMaxProjWin + uu[1]] * gg,
-                            ds[2 * kMaxProjWin + uu[2]] * gg};
+            R f[4];
+            PVal<R>::get(P, e, f);
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
-                const R sh = f[l] * Ct[4LL * at + l];
-                y.x += sh * (R)S.c[k][l].x;
-                y.y += sh * (R)S.c[k][l].y;
+                const auto cc = PVal<R>::c(S, k, l);
+                yx += f[l] * (R)cc.x;
+                yy += f[l] * (R)cc.y;
             }
         }
     }
-    return y;
+    return cmake<C>(yx, yy);
 }
 
-template <class Mode>
+template <class Mode, int Q>
 __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolveParams P) {
     using R = typename Mode::real;
     using C = typename Mode::cplx;
     __shared__ Shared S;
     const uint64_t t_start = global_time_ns();
     char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
+    for (int t = threadIdx.x; t < 3 * kMaxQ; t += blockDim.x) {
+        (&S.coefD[0][0])[t] = (&P.coef[0][0])[t];
+        (&S.coefF[0][0])[t] = (float)(&P.coef[0][0])[t];
+    }
+    if (P.nonlocal && P.n_atoms <= kMapMax)
+        for (int t = threadIdx.x; t < P.n_atoms; t += blockDim.x) S.map[t] = -1;
+    const R diagR = (R)P.diag;
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -325,19 +406,23 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
         if (s >= P.n_sys) break;
         const SysDesc sd = P.sys[s];
         const NodeDesc nd = P.nodes[sd.node];
-        RegionGeo G;
+        Geo G;
+        G.any_ring = 0;
         for (int d = 0; d < 3; ++d) {
             G.m[d] = nd.dims[d];
             G.lo[d] = nd.lo[d];
             G.ring[d] = (nd.ring >> d) & 1;
+            G.any_ring |= G.ring[d];
         }
-        G.n = G.m[0] * G.m[1] * G.m[2];
+        G.plane = G.m[0] * G.m[1];
+        G.n = G.plane * G.m[2];
         G.src = nd.src;
+        G.div_row = make_fastdiv((uint32_t)G.m[0]);
+        G.div_plane = make_fastdiv((uint32_t)G.plane);
         const double2 zd = P.z[sd.pole];
-        const C z = cmake<C>((R)zd.x, (R)zd.y);
+        const R zr = (R)zd.x, zi = (R)zd.y;
         const long long out_idx = (long long)sd.node * P.P + sd.pole;
 
-        // vectors
         C* r = (C*)slot;
         C* p = r + P.n_max;
         C* Ap = p + P.n_max;
@@ -348,8 +433,7 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
         if (P.nonlocal) collect_local_atoms(P, G, S);
 
         for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
-            const R one = (i == G.src) ? (R)1 : (R)0;
-            r[i] = cmake<C>(one, (R)0);
+            r[i] = cmake<C>((R)(i == G.src ? 1 : 0), (R)0);
             p[i] = cmake<C>((R)0, (R)0);
             x[i] = make_double2(0.0, 0.0);
             if (Mode::kMixed) dx[i] = cmake<C>((R)0, (R)0);
@@ -368,8 +452,7 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                 timed_out = true;
                 break;
             }
-            // P1: p = r + beta p
-            {
+            {   // P1: p = r + beta p
                 const R br = (R)beta_re, bi = (R)beta_im;
                 for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
                     const C ri = r[i], pi = p[i];
@@ -378,15 +461,11 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
             }
             __syncthreads();
             if (P.nonlocal) nonlocal_coeffs<R, C>(P, G, S, p);
-            // P2: Ap = (H_R - z) p ; p^T Ap
             double pap[2];
-            {
+            {   // P2: Ap = (H_R - z) p ; p^T Ap
                 R acc_re = 0, acc_im = 0;
                 for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
-                    const int a = i % G.m[0];
-                    const int b = (i / G.m[0]) % G.m[1];
-                    const int c = i / (G.m[0] * G.m[1]);
-                    const C y = apply_point<R, C, C>(P, G, S, p, i, a, b, c, z);
+                    const C y = matvec_point<R, C, Q, C>(P, G, S, p, i, zr, zi, diagR);
                     Ap[i] = y;
                     const C pi = p[i];
                     acc_re += pi.x * y.x - pi.y * y.y;
@@ -404,9 +483,8 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
             }
             const double al_re = (rho_re * pap[0] + rho_im * pap[1]) / den;
             const double al_im = (rho_im * pap[0] - rho_re * pap[1]) / den;
-            // P3: x += alpha p ; r -= alpha Ap ; r^T r ; |r|^2
             double red3[3];
-            {
+            {   // P3: x += alpha p ; r -= alpha Ap ; r^T r ; |r|^2
                 const R ar = (R)al_re, ai = (R)al_im;
                 R s_re = 0, s_im = 0, s_n = 0;
                 for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
@@ -452,18 +530,15 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                     __syncthreads();
                     if (P.nonlocal) nonlocal_coeffs<double, double2>(P, G, S, x);
                     double t3[3] = {0, 0, 0};
-                    const double2 z64 = zd;
                     for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
-                        const int a = i % G.m[0];
-                        const int b = (i / G.m[0]) % G.m[1];
-                        const int c = i / (G.m[0] * G.m[1]);
-                        const double2 y = apply_point<double, double2, double2>(P, G, S, x, i, a, b, c, z64);
+                        const double2 y =
+                            matvec_point<double, double2, Q, double2>(P, G, S, x, i, zd.x, zd.y, P.diag);
                         const double tre = (i == G.src ? 1.0 : 0.0) - y.x;
                         const double tim = -y.y;
-                        r[i] = cmake<C>((R)tre, (R)tim);
-                        const R rr = (R)tre, ri = (R)tim;
-                        t3[0] += (double)(rr * rr - ri * ri);
-                        t3[1] += (double)(2 * rr * ri);
+                        const C rr = cmake<C>((R)tre, (R)tim);
+                        r[i] = rr;
+                        t3[0] += (double)(rr.x * rr.x - rr.y * rr.y);
+                        t3[1] += (double)(2 * rr.x * rr.y);
                         t3[2] += tre * tre + tim * tim;
                     }
                     block_sum<3>(S, t3);
@@ -491,7 +566,6 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
             rho_im = red3[1];
         }
         if (Mode::kMixed && status != 0) {
-            // leave x_hi consistent with the iterate reached
             for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
                 const C d = dx[i];
                 double2 xv = x[i];
@@ -508,6 +582,7 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
             P.resid[out_idx] = rn;
             P.n_rel[out_idx] = n_rel;
         }
+        if (P.nonlocal) release_local_atoms(P, S);
         __syncthreads();
     }
 }
@@ -522,12 +597,10 @@ __global__ void k_accumulate(int n_nodes, int Pn, const double2* __restrict__ x_
     for (int p = 0; p < Pn; ++p) {
         const double2 xv = x_src[(long long)j * Pn + p];
         const double2 ww = w[p], zz = z[p];
-        // Im(w x)
-        sr += ww.x * xv.y + ww.y * xv.x;
-        // Im(w (1 + z x))
+        sr += ww.x * xv.y + ww.y * xv.x;                       // Im(w x)
         const double zx_re = zz.x * xv.x - zz.y * xv.y;
         const double zx_im = zz.x * xv.y + zz.y * xv.x;
-        se += ww.y + ww.x * zx_im + ww.y * zx_re;
+        se += ww.y + ww.x * zx_im + ww.y * zx_re;              // Im(w (1 + z x))
     }
     rho[j] = (2.0 / dV) * sr;
     if (e) e[j] = 2.0 * se;
@@ -544,6 +617,22 @@ struct MixedMode {
     static constexpr bool kMixed = true;
 };
 
+template <class Mode>
+cudaError_t launch_q(const SolveParams& P, int grid, int block, cudaStream_t stream) {
+    switch (P.q) {
+        case 1: k_cocg<Mode, 1><<<grid, block, 0, stream>>>(P); break;
+        case 2: k_cocg<Mode, 2><<<grid, block, 0, stream>>>(P); break;
+        case 3: k_cocg<Mode, 3><<<grid, block, 0, stream>>>(P); break;
+        case 4: k_cocg<Mode, 4><<<grid, block, 0, stream>>>(P); break;
+        case 5: k_cocg<Mode, 5><<<grid, block, 0, stream>>>(P); break;
+        case 6: k_cocg<Mode, 6><<<grid, block, 0, stream>>>(P); break;
+        case 7: k_cocg<Mode, 7><<<grid, block, 0, stream>>>(P); break;
+        case 8: k_cocg<Mode, 8><<<grid, block, 0, stream>>>(P); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t slot_bytes_for(int precision, long long n_max) {
@@ -553,12 +642,8 @@ size_t slot_bytes_for(int precision, long long n_max) {
 }
 
 cudaError_t launch_cocg(const SolveParams& P, int precision, int grid, int block, cudaStream_t stream) {
-    if (precision == MD_PREC_MIXED) {
-        k_cocg<MixedMode><<<grid, block, 0, stream>>>(P);
-    } else {
-        k_cocg<FP64Mode><<<grid, block, 0, stream>>>(P);
-    }
-    return cudaGetLastError();
+    if (precision == MD_PREC_MIXED) return launch_q<MixedMode>(P, grid, block, stream);
+    return launch_q<FP64Mode>(P, grid, block, stream);
 }
 
 cudaError_t launch_accumulate(int n_nodes, int Pn, const double2* x_src, const double2* z,

@@ -44,8 +44,10 @@ struct SolveParams {
     const double* proj_C;
     const float* proj_C32;
     const unsigned char* proj_rows;
-    const long long* pl_ptr;
+    const int* pl_ptr;
     const int* pl_atom;
+    const float4* pl_val32;
+    const double2* pl_val64;
     double e_s, e_p;
     // systems
     int n_sys;
