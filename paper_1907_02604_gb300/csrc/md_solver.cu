@@ -47,6 +47,8 @@ namespace {
 
 constexpr int kLocal = kMaxLocalProjAtoms;
 constexpr int kMapMax = 4096;   // direct global->local atom map when n_atoms <= this
+constexpr int kChunk = 8;       // points per FP32 partial sum before it joins the FP64 sum
+constexpr int kStop = 1, kRefresh = 2, kStopTimeout = 3;
 
 struct FastDiv {
     uint32_t m;
@@ -96,6 +98,10 @@ struct Shared {
     double bcast[4];
     double coefD[3][kMaxQ];
     float coefF[3][kMaxQ];
+    double alpha[2];
+    double beta[2];
+    int action;
+    int status;
     int sys;
     int flag;
     int n_local;
@@ -112,6 +118,26 @@ template <>
 __device__ __forceinline__ const double* coef_of<double>(const Shared& S) { return &S.coefD[0][0]; }
 template <>
 __device__ __forceinline__ const float* coef_of<float>(const Shared& S) { return &S.coefF[0][0]; }
+
+// Block-wide sum of K doubles; only thread 0 holds the totals afterwards.
+template <int K>
+__device__ __forceinline__ void block_reduce(Shared& S, double (&v)[K]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) S.red[warp][k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = lane < nw ? S.red[lane][k] : 0.0;
+            v[k] = warp_sum(t);
+        }
+    }
+}
 
 template <int K>
 __device__ __forceinline__ void block_sum(Shared& S, double (&v)[K]) {
@@ -142,11 +168,36 @@ __device__ __forceinline__ int wrap_once(int g, int n) {
     return g;
 }
 
-// Region slot of window index u for an atom window starting at region offset off.
-__device__ __forceinline__ int region_slot(int off, int u, int n, int m) {
+// Region slot of window index u for an atom window starting at region
+// offset off (periodic axes: off in [0, n) and the window may wrap once).
+__device__ __forceinline__ int region_slot(int off, int u, int n, int m, int periodic) {
     int a = off + u;
-    if (a >= n) a -= n;
+    if (periodic && a >= n) a -= n;
     return (a >= 0 && a < m) ? a : -1;
+}
+
+// The window indices u in [0, len) that land in the region on one axis form
+// at most two runs; run k covers u in [lo_k, hi_k] with region slot u + shift_k.
+struct Runs {
+    int lo[2], hi[2], shift[2];
+};
+
+__device__ __forceinline__ Runs axis_runs(int off, int len, int n, int m, int periodic) {
+    Runs r;
+    r.lo[0] = max(0, -off);
+    r.hi[0] = min(len - 1, m - 1 - off);
+    if (periodic) r.hi[0] = min(r.hi[0], n - 1 - off);
+    r.shift[0] = off;
+    if (periodic) {
+        r.lo[1] = max(0, n - off);
+        r.hi[1] = min(len - 1, n - off + m - 1);
+        r.shift[1] = off - n;
+    } else {
+        r.lo[1] = 1;
+        r.hi[1] = 0;
+        r.shift[1] = 0;
+    }
+    return r;
 }
 
 // Local atoms whose projector window meets the region; ascending atom id.
@@ -213,11 +264,13 @@ __device__ __forceinline__ int local_slot(const SolveParams& P, const Shared& S,
     return -1;
 }
 
-// c_al = E_l dV sum_{i in region} p_al(i) v(i) (warp per atom, two rows per step).
+// c_al = E_l dV sum_{i in region} p_al(i) v(i): warp per local atom, lane
+// per window row (v, w).  The Gaussian is separable, so each row needs only
+// A = sum_u g_x(u) v and B = sum_u d_x(u) g_x(u) v over its in-sphere run:
+//   c_s += g_y g_z A, c_x += g_y g_z B, c_y += d_y g_y g_z A, c_z += d_z g_y g_z A.
 template <class R, class C>
 __device__ void nonlocal_coeffs(const SolveParams& P, const Geo& G, Shared& S, const C* __restrict__ v) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int half = lane >> 4, hl = lane & 15;
     const R* dt = Tab<R>::d(P);
     const R* gt = Tab<R>::g(P);
     for (int k = warp; k < S.n_local; k += nw) {
@@ -231,31 +284,35 @@ __device__ void nonlocal_coeffs(const SolveParams& P, const Geo& G, Shared& S, c
         const R* gy = gt + (3LL * a + 1) * kMaxProjWin;
         const R* gz = gt + (3LL * a + 2) * kMaxProjWin;
         const unsigned char* rows = P.proj_rows + 2LL * a * kMaxProjWin * kMaxProjWin;
+        const Runs rx = axis_runs(S.la_off[k][0], lx, P.n[0], G.m[0], P.periodic[0]);
         R acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         const int nrows = ly * lz;
-        for (int r0 = 0; r0 < nrows; r0 += 2) {
-            const int row = r0 + half;
-            if (row >= nrows) continue;
+        for (int row = lane; row < nrows; row += 32) {
             const int ww = row / ly, vv = row - ww * ly;
-            const int b = region_slot(S.la_off[k][1], vv, P.n[1], G.m[1]);
-            const int c = region_slot(S.la_off[k][2], ww, P.n[2], G.m[2]);
+            const int b = region_slot(S.la_off[k][1], vv, P.n[1], G.m[1], P.periodic[1]);
+            const int c = region_slot(S.la_off[k][2], ww, P.n[2], G.m[2], P.periodic[2]);
             if (b < 0 || c < 0) continue;
             const unsigned char* rw = rows + 2 * (ww * kMaxProjWin + vv);
-            const int u0 = rw[0], u1 = min((int)rw[1], lx - 1);
-            const R gyz = __ldg(gy + vv) * __ldg(gz + ww);
-            const R ey = __ldg(dy + vv), ez = __ldg(dz + ww);
-            const int base_i = G.m[0] * (b + G.m[1] * c);
-            for (int u = u0 + hl; u <= u1; u += 16) {
-                const int aa = region_slot(S.la_off[k][0], u, P.n[0], G.m[0]);
-                if (aa < 0) continue;
-                const C pv = v[base_i + aa];
-                const R gg = __ldg(gx + u) * gyz;
-                const R f1 = __ldg(dx + u) * gg, f2 = ey * gg, f3 = ez * gg;
-                acc[0] += gg * (R)pv.x; acc[1] += gg * (R)pv.y;
-                acc[2] += f1 * (R)pv.x; acc[3] += f1 * (R)pv.y;
-                acc[4] += f2 * (R)pv.x; acc[5] += f2 * (R)pv.y;
-                acc[6] += f3 * (R)pv.x; acc[7] += f3 * (R)pv.y;
+            const int u0 = rw[0], u1 = rw[1];
+            const C* vrow = v + G.m[0] * (b + G.m[1] * c);
+            R Ar = 0, Ai = 0, Br = 0, Bi = 0;
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int lo = max(u0, rx.lo[t]), hi = min(u1, rx.hi[t]);
+                for (int u = lo; u <= hi; ++u) {
+                    const C pv = vrow[u + rx.shift[t]];
+                    const R g1 = __ldg(gx + u);
+                    const R g2 = __ldg(dx + u) * g1;
+                    Ar += g1 * (R)pv.x; Ai += g1 * (R)pv.y;
+                    Br += g2 * (R)pv.x; Bi += g2 * (R)pv.y;
+                }
             }
+            const R gyz = __ldg(gy + vv) * __ldg(gz + ww);
+            const R ey = __ldg(dy + vv) * gyz, ez = __ldg(dz + ww) * gyz;
+            acc[0] += gyz * Ar; acc[1] += gyz * Ai;
+            acc[2] += gyz * Br; acc[3] += gyz * Bi;
+            acc[4] += ey * Ar;  acc[5] += ey * Ai;
+            acc[6] += ez * Ar;  acc[7] += ez * Ai;
         }
         double s[8];
 #pragma unroll
@@ -440,20 +497,26 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
         }
         __syncthreads();
 
+        // Scalar state lives in thread 0; the others see it through S.
         double rho_re = 1.0, rho_im = 0.0;   // r^T r
-        double beta_re = 0.0, beta_im = 0.0;
         double rn = 1.0, rn_last_rel = 1.0;
         int it = 0, last_rel = 0, n_rel = 0;
         int status = 2;  // not converged
-        bool timed_out = false;
+        if (threadIdx.x == 0) {
+            S.beta[0] = 0.0;
+            S.beta[1] = 0.0;
+            S.action = 0;
+        }
+        __syncthreads();
 
-        while (it < P.maxit) {
-            if (P.timeout_ns && (global_time_ns() - t_start) > P.timeout_ns) {
-                timed_out = true;
-                break;
-            }
+        for (;;) {
+            if (P.timeout_ns && threadIdx.x == 0 && (global_time_ns() - t_start) > P.timeout_ns)
+                S.action = kStopTimeout;
+            if (threadIdx.x == 0 && it >= P.maxit) S.action = kStop;
+            __syncthreads();
+            if (S.action == kStop || S.action == kStopTimeout) break;
             {   // P1: p = r + beta p
-                const R br = (R)beta_re, bi = (R)beta_im;
+                const R br = (R)S.beta[0], bi = (R)S.beta[1];
                 for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
                     const C ri = r[i], pi = p[i];
                     p[i] = cmake<C>(ri.x + br * pi.x - bi * pi.y, ri.y + br * pi.y + bi * pi.x);
@@ -461,32 +524,46 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
             }
             __syncthreads();
             if (P.nonlocal) nonlocal_coeffs<R, C>(P, G, S, p);
-            double pap[2];
             {   // P2: Ap = (H_R - z) p ; p^T Ap
+                double pap[2] = {0.0, 0.0};
                 R acc_re = 0, acc_im = 0;
+                int cnt = 0;
                 for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
                     const C y = matvec_point<R, C, Q, C>(P, G, S, p, i, zr, zi, diagR);
                     Ap[i] = y;
                     const C pi = p[i];
                     acc_re += pi.x * y.x - pi.y * y.y;
                     acc_im += pi.x * y.y + pi.y * y.x;
+                    if (++cnt == kChunk) {   // short FP32 runs, FP64 above them
+                        pap[0] += (double)acc_re;
+                        pap[1] += (double)acc_im;
+                        acc_re = acc_im = 0;
+                        cnt = 0;
+                    }
                 }
-                pap[0] = (double)acc_re;
-                pap[1] = (double)acc_im;
-                block_sum<2>(S, pap);
+                pap[0] += (double)acc_re;
+                pap[1] += (double)acc_im;
+                block_reduce<2>(S, pap);
+                if (threadIdx.x == 0) {
+                    ++it;
+                    const double den = pap[0] * pap[0] + pap[1] * pap[1];
+                    if (!(den > 0.0)) {
+                        status = 3;
+                        S.action = kStop;
+                    } else {
+                        S.alpha[0] = (rho_re * pap[0] + rho_im * pap[1]) / den;
+                        S.alpha[1] = (rho_im * pap[0] - rho_re * pap[1]) / den;
+                    }
+                }
+                __syncthreads();
+                if (S.action == kStop) break;
             }
-            ++it;
-            const double den = pap[0] * pap[0] + pap[1] * pap[1];
-            if (!(den > 0.0)) {
-                status = 3;
-                break;
-            }
-            const double al_re = (rho_re * pap[0] + rho_im * pap[1]) / den;
-            const double al_im = (rho_im * pap[0] - rho_re * pap[1]) / den;
-            double red3[3];
+            double red3[3] = {0.0, 0.0, 0.0};
             {   // P3: x += alpha p ; r -= alpha Ap ; r^T r ; |r|^2
+                const double al_re = S.alpha[0], al_im = S.alpha[1];
                 const R ar = (R)al_re, ai = (R)al_im;
                 R s_re = 0, s_im = 0, s_n = 0;
+                int cnt = 0;
                 for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
                     const C pi = p[i], api = Ap[i];
                     if (Mode::kMixed) {
@@ -507,17 +584,28 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                     s_re += ri.x * ri.x - ri.y * ri.y;
                     s_im += 2 * ri.x * ri.y;
                     s_n += ri.x * ri.x + ri.y * ri.y;
+                    if (++cnt == kChunk) {
+                        red3[0] += (double)s_re;
+                        red3[1] += (double)s_im;
+                        red3[2] += (double)s_n;
+                        s_re = s_im = s_n = 0;
+                        cnt = 0;
+                    }
                 }
-                red3[0] = (double)s_re;
-                red3[1] = (double)s_im;
-                red3[2] = (double)s_n;
-                block_sum<3>(S, red3);
+                red3[0] += (double)s_re;
+                red3[1] += (double)s_im;
+                red3[2] += (double)s_n;
+                block_reduce<3>(S, red3);
             }
-            rn = sqrt(red3[2]);
             if (Mode::kMixed) {
-                const bool want = (rn <= P.tol) || (it - last_rel >= P.reliable_every) ||
-                                  (rn < P.reliable_delta * rn_last_rel);
-                if (want) {
+                if (threadIdx.x == 0) {
+                    rn = sqrt(red3[2]);
+                    const bool want = (rn <= P.tol) || (it - last_rel >= P.reliable_every) ||
+                                      (rn < P.reliable_delta * rn_last_rel);
+                    S.action = want ? kRefresh : 0;
+                }
+                __syncthreads();
+                if (S.action == kRefresh) {
                     // flush dx into x_hi, then r = e_j - (H_R - z) x_hi in FP64
                     for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
                         const C d = dx[i];
@@ -541,30 +629,42 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                         t3[1] += (double)(2 * rr.x * rr.y);
                         t3[2] += tre * tre + tim * tim;
                     }
-                    block_sum<3>(S, t3);
-                    red3[0] = t3[0];
-                    red3[1] = t3[1];
-                    rn = sqrt(t3[2]);
-                    rn_last_rel = rn;
-                    last_rel = it;
-                    ++n_rel;
+                    block_reduce<3>(S, t3);
+                    if (threadIdx.x == 0) {
+                        red3[0] = t3[0];
+                        red3[1] = t3[1];
+                        red3[2] = t3[2];
+                        rn_last_rel = sqrt(t3[2]);
+                        last_rel = it;
+                        ++n_rel;
+                    }
                 }
             }
-            if (rn <= P.tol) {
-                status = 0;
-                break;
+            if (threadIdx.x == 0) {
+                rn = sqrt(red3[2]);
+                S.action = 0;
+                const double rr_abs = sqrt(red3[0] * red3[0] + red3[1] * red3[1]);
+                if (rn <= P.tol) {
+                    status = 0;
+                    S.action = kStop;
+                } else if (!(rr_abs > 1e-300) || rr_abs < 1e-14 * rn * rn) {
+                    status = 3;
+                    S.action = kStop;
+                } else {
+                    const double rd = rho_re * rho_re + rho_im * rho_im;
+                    S.beta[0] = (red3[0] * rho_re + red3[1] * rho_im) / rd;
+                    S.beta[1] = (red3[1] * rho_re - red3[0] * rho_im) / rd;
+                    rho_re = red3[0];
+                    rho_im = red3[1];
+                }
             }
-            const double rr_abs = sqrt(red3[0] * red3[0] + red3[1] * red3[1]);
-            if (!(rr_abs > 1e-300) || rr_abs < 1e-14 * rn * rn) {
-                status = 3;
-                break;
-            }
-            const double rd = rho_re * rho_re + rho_im * rho_im;
-            beta_re = (red3[0] * rho_re + red3[1] * rho_im) / rd;
-            beta_im = (red3[1] * rho_re - red3[0] * rho_im) / rd;
-            rho_re = red3[0];
-            rho_im = red3[1];
+            __syncthreads();
+            if (S.action == kStop) break;
         }
+        const bool timed_out = (S.action == kStopTimeout);
+        if (threadIdx.x == 0) S.status = status;
+        __syncthreads();
+        status = S.status;
         if (Mode::kMixed && status != 0) {
             for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
                 const C d = dx[i];
