@@ -199,6 +199,33 @@ md_status md_energy(const md_hamiltonian* ham, const md_poles* poles,
                     const md_nodes* nodes, const md_solver_opts* opts,
                     double* e_out, double* e_band, md_stats* stats, void* stream);
 
+/* ---- Plans: a prepared batched solve replayed as a CUDA graph ----------
+ * md_plan_create validates the inputs once, uploads the cost-sorted
+ * (node, pole) work list and region descriptors, allocates the plan's own
+ * Krylov scratch and per-system outputs, picks the launch shape (threads
+ * per CTA and CTAs per SM; timed by the library's autotuner on a sample of
+ * the systems when opts->block == 0, cached per precision, stencil width,
+ * region size and nonlocal term) and captures [reset the work counter,
+ * the persistent solver kernel, the pole accumulation into rho_out/e_out]
+ * as one CUDA graph.  The pointers given here (rho_out, e_out, ckpt, the
+ * Hamiltonian's arrays) are baked into the graph: they must stay valid
+ * until md_plan_destroy; md_hamiltonian_set_potential between launches is
+ * seen by the next launch.  Creation synchronises `stream` (autotuning);
+ * md_plan_launch is asynchronous (one cudaGraphLaunch); md_plan_stats
+ * synchronises `stream` and returns the status of the last launch
+ * (MD_ERR_NOCONV / MD_ERR_BREAKDOWN / MD_ERR_TIMEOUT as for md_density).
+ * A plan may not be launched concurrently with itself. */
+typedef struct md_plan md_plan;
+md_status md_plan_create(const md_hamiltonian* ham, const md_poles* poles,
+                         const md_nodes* nodes, const md_solver_opts* opts,
+                         double* rho_out, double* e_out, md_workspace* ckpt,
+                         void* stream, md_plan** out);
+md_status md_plan_launch(md_plan* plan, void* stream);
+md_status md_plan_stats(md_plan* plan, void* stream, md_stats* stats);
+/* Launch shape chosen for the plan (threads per CTA, CTAs in the grid). */
+md_status md_plan_launch_shape(const md_plan* plan, int32_t* block, int32_t* grid);
+md_status md_plan_destroy(md_plan* plan);
+
 /* Adjoint of (rho, e) -> L.  With a_j = dL/drho_j and b_j = dL/de_j:
  *   dL/dV_k = -sum_j sum_p Im((2 a_j/dV + 2 b_j z_p) w_p x_jp(k)^2)
  * (G = (H_R - z)^-1 is complex symmetric, so dG_jj/dV_k = -x_jp(k)^2 and

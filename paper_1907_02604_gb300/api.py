@@ -193,6 +193,58 @@ class Workspace:
 _SOFT = (_lib.MD_ERR_NOCONV, _lib.MD_ERR_BREAKDOWN)
 
 
+class Plan:
+    """A prepared batched solve replayed as one CUDA graph (md_plan_*).
+
+    The output tensors rho (and e) are owned by the plan object and
+    rewritten by every launch."""
+
+    def __init__(self, ham: Hamiltonian, z, w, nodes, halfwidth, opts: SolverOptions = None,
+                 energy=True, checkpoint: Workspace = None, stream=None):
+        opts = opts or SolverOptions()
+        self._poles, self._nodes = _PoleArgs(z, w), _NodeArgs(nodes, halfwidth)
+        self.rho = torch.empty(self._nodes.n, dtype=torch.float64, device="cuda")
+        self.e = torch.empty(self._nodes.n, dtype=torch.float64, device="cuda") if energy else None
+        self._opts = opts.to_c()
+        self._ham = ham          # keep the Hamiltonian alive as long as the graph
+        self._ckpt = checkpoint
+        h = ctypes.c_void_p()
+        check(load().md_plan_create(ham.handle, ctypes.byref(self._poles.c), ctypes.byref(self._nodes.c),
+                                    ctypes.byref(self._opts), ctypes.c_void_p(self.rho.data_ptr()),
+                                    ctypes.c_void_p(self.e.data_ptr()) if self.e is not None else None,
+                                    checkpoint.handle if checkpoint is not None else None,
+                                    _stream_handle(stream), ctypes.byref(h)), "md_plan_create")
+        self._h = h
+        self.n_systems = self._nodes.n * self._poles.P
+
+    def launch(self, stream=None):
+        check(load().md_plan_launch(self._h, _stream_handle(stream)), "md_plan_launch")
+
+    def stats(self, stream=None, strict=True):
+        st = _lib.md_stats()
+        status = load().md_plan_stats(self._h, _stream_handle(stream), ctypes.byref(st))
+        check(status, "md_plan_stats", allow=() if strict else _SOFT)
+        d = st.as_dict()
+        d["status"] = _lib.STATUS_NAMES[status]
+        return d
+
+    def launch_shape(self):
+        b, g = ctypes.c_int32(), ctypes.c_int32()
+        check(load().md_plan_launch_shape(self._h, ctypes.byref(b), ctypes.byref(g)), "md_plan_launch_shape")
+        return b.value, g.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().md_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def density(ham: Hamiltonian, z, w, nodes, halfwidth, opts: SolverOptions = None, energy=False,
             checkpoint: Workspace = None, out=None, stream=None, strict=True):
     """rho_j (and e_j) for every node.  Returns (rho, e or None, stats dict).

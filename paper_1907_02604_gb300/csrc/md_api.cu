@@ -186,47 +186,216 @@ md_status check_opts(const md_solver_opts* o) {
     return MD_OK;
 }
 
-// Solve every (node, pole) system; outputs x_src (device, n_nodes*P).
-md_status run_solver(Ham& H, const md_poles* poles, const Regions& R, const md_solver_opts* opts_in,
-                     double2* d_xsrc, md_workspace* ckpt, md_stats* stats, cudaStream_t stream,
-                     const double2* d_z) {
-    md_status st = MD_OK;
-    const md_solver_opts opts = normalise_opts(opts_in);
+md_status upload_poles(const md_poles* poles, double2** d_z, double2** d_w, cudaStream_t stream) {
     const int Pn = poles->n_poles;
-    const long long nn = (long long)R.desc.size();
-    const long long n_sys = nn * Pn;
-    int dev = 0, n_sm = 0;
-    SysDesc* d_sys = nullptr;
-    NodeDesc* d_nodes = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)d_z, Pn * sizeof(double2), stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)d_w, Pn * sizeof(double2), stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(*d_z, poles->z, Pn * sizeof(double2), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(*d_w, poles->w, Pn * sizeof(double2), cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    return MD_OK;
+}
+
+}  // namespace
+}  // namespace md
+
+// ---------------------------------------------------------------------------
+// Plans: one prepared batched solve, replayed as a CUDA graph.
+// ---------------------------------------------------------------------------
+struct md_plan {
+    md::Ham* H = nullptr;
+    int precision = 0;
+    int Pn = 0;
+    long long nn = 0;
+    long long n_sys = 0;
+    int grid = 0, block = 0;
+    std::vector<long long> points;     // region points per node
+    md::SolveParams P;
+    // device buffers owned by the plan
+    void* scratch = nullptr;
+    bool own_scratch = true;
+    md::SysDesc* d_sys = nullptr;
+    md::NodeDesc* d_nodes = nullptr;
     long long* d_ckoff = nullptr;
     int* d_status = nullptr;
     int* d_iters = nullptr;
     int* d_nrel = nullptr;
     double* d_resid = nullptr;
+    double2* d_xsrc = nullptr;
+    double2* d_z = nullptr;
+    double2* d_w = nullptr;
     unsigned int* d_counter = nullptr;
+    double* rho_out = nullptr;
+    double* e_out = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    std::vector<SysDesc> sys;
-    std::vector<long long> ckoff;
-    std::vector<int> h_status, h_iters, h_nrel;
-    std::vector<double> h_resid;
-    SolveParams P;
-    int block, per_sm, grid;
-    size_t slot, need;
-    long long n_max_r;
-    float ms = 0.f;
-    std::memset(&P, 0, sizeof(P));
-    if (n_sys == 0) {
-        if (stats) {
-            std::memset(stats, 0, sizeof(*stats));
+    bool launched = false;
+};
+
+namespace md {
+namespace {
+
+#define PLAN_TRY(expr)                                                                    \
+    do {                                                                                  \
+        cudaError_t _e = (expr);                                                          \
+        if (_e != cudaSuccess) {                                                          \
+            return set_error((_e == cudaErrorMemoryAllocation) ? MD_ERR_OOM : MD_ERR_CUDA, \
+                             std::string("CUDA: ") + cudaGetErrorString(_e) + " (" #expr ")"); \
+        }                                                                                 \
+    } while (0)
+
+void plan_free(md_plan* pl) {
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->cap) cudaStreamDestroy(pl->cap);
+    if (pl->ev0) cudaEventDestroy(pl->ev0);
+    if (pl->ev1) cudaEventDestroy(pl->ev1);
+    void* ptrs[] = {pl->d_sys, pl->d_nodes, pl->d_ckoff, pl->d_status, pl->d_iters, pl->d_nrel,
+                    pl->d_resid, pl->d_xsrc, pl->d_z, pl->d_w, pl->d_counter};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (pl->own_scratch && pl->scratch) cudaFree(pl->scratch);
+    delete pl;
+}
+
+// Launch-shape autotuner: times each candidate (threads per CTA, CTAs per
+// SM) on the same evenly spread sample of systems with a short iteration
+// cap and keeps the one with the most region-point iterations per second.
+// Results are cached per (precision, stencil width, region-size bucket,
+// nonlocal) for the life of the process.
+struct TuneKey {
+    int precision, q, bucket, nonlocal;
+    bool operator==(const TuneKey& o) const {
+        return precision == o.precision && q == o.q && bucket == o.bucket && nonlocal == o.nonlocal;
+    }
+};
+struct TuneEntry {
+    TuneKey key;
+    int block, per_sm;
+};
+std::vector<TuneEntry> g_tune_cache;
+
+md_status autotune(md_plan* pl, int n_sm, int& block_out, int& per_sm_out) {
+    const TuneKey key{pl->precision, pl->P.q, (int)((pl->P.n_max + 8191) / 8192), pl->P.nonlocal};
+    for (const auto& e : g_tune_cache)
+        if (e.key == key) {
+            block_out = e.block;
+            per_sm_out = e.per_sm;
+            return MD_OK;
         }
+    const int cand[][2] = {{1024, 1}, {512, 2}, {768, 1}, {256, 4}, {512, 1}};
+    // sample: up to n_sm systems spread evenly over the cost-sorted list
+    const long long ns = std::min<long long>(pl->n_sys, n_sm);
+    std::vector<SysDesc> all(pl->n_sys), sample;
+    PLAN_TRY(cudaMemcpy(all.data(), pl->d_sys, pl->n_sys * sizeof(SysDesc), cudaMemcpyDeviceToHost));
+    for (long long k = 0; k < ns; ++k) sample.push_back(all[(k * pl->n_sys) / ns]);
+    SysDesc* d_sample = nullptr;
+    PLAN_TRY(cudaMalloc(&d_sample, ns * sizeof(SysDesc)));
+    cudaMemcpy(d_sample, sample.data(), ns * sizeof(SysDesc), cudaMemcpyHostToDevice);
+    double best = -1.0;
+    int bb = 512, bp = 2;
+    for (const auto& c : cand) {
+        SolveParams T = pl->P;
+        T.sys = d_sample;
+        T.n_sys = (int)ns;
+        T.maxit = std::min(pl->P.maxit, 48);
+        T.ckpt = nullptr;   // trials never touch the checkpoint
+        const int grid = (int)std::min<long long>((long long)n_sm * c[1], ns);
+        const size_t need = pl->P.slot_bytes * (size_t)grid;
+        size_t have = pl->own_scratch ? pl->P.slot_bytes * (size_t)pl->grid : pl->H->scratch_bytes;
+        if (need > have) continue;
+        cudaMemset(T.work_counter, 0, sizeof(unsigned int));
+        cudaEventRecord(pl->ev0, pl->cap);
+        cudaError_t e = launch_cocg(T, pl->precision, grid, c[0], pl->cap);
+        cudaEventRecord(pl->ev1, pl->cap);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (cudaStreamSynchronize(pl->cap) != cudaSuccess) {
+            cudaFree(d_sample);
+            return set_error(MD_ERR_CUDA, "autotune trial failed");
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, pl->ev0, pl->ev1);
+        // work done: the trial writes iters at indices node*P + pole of the sample
+        long long pit = 0;
+        std::vector<int> h_it(pl->n_sys);
+        cudaMemcpy(h_it.data(), T.iters, pl->n_sys * sizeof(int), cudaMemcpyDeviceToHost);
+        for (const auto& sd : sample) pit += (long long)h_it[(long long)sd.node * pl->Pn + sd.pole] * pl->points[sd.node];
+        const double rate = ms > 0 ? (double)pit / ms : 0.0;
+        if (rate > best) {
+            best = rate;
+            bb = c[0];
+            bp = c[1];
+        }
+    }
+    cudaFree(d_sample);
+    g_tune_cache.push_back(TuneEntry{key, bb, bp});
+    block_out = bb;
+    per_sm_out = bp;
+    return MD_OK;
+}
+
+md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,
+                      const md_solver_opts* opts_in, double* rho_out, double* e_out, md_workspace* ckpt,
+                      bool borrow_scratch, cudaStream_t stream, md_plan** out) {
+    *out = nullptr;
+    md_status st = check_device();
+    if (st != MD_OK) return st;
+    if (!ham) return set_error(MD_ERR_INVALID, "ham is NULL");
+    if ((st = check_poles(poles)) != MD_OK) return st;
+    if ((st = check_opts(opts_in)) != MD_OK) return st;
+    Ham& H = const_cast<md_hamiltonian*>(ham)->h;
+    Regions R;
+    if ((st = make_regions(H, nodes, R)) != MD_OK) return st;
+    const long long nn = (long long)R.desc.size();
+    if (!rho_out && nn > 0) return set_error(MD_ERR_INVALID, "rho_out is NULL");
+    if (ckpt && (ckpt->n_nodes != nn || ckpt->n_poles != poles->n_poles || ckpt->total_points != R.total))
+        return set_error(MD_ERR_INVALID, "checkpoint workspace was made for other nodes or poles");
+    const md_solver_opts opts = normalise_opts(opts_in);
+    const int Pn = poles->n_poles;
+    const long long n_sys = nn * Pn;
+    if (n_sys > (1LL << 31) - 1) return set_error(MD_ERR_INVALID, "too many systems");
+
+    md_plan* pl = new md_plan();
+    pl->H = &H;
+    pl->precision = opts.precision;
+    pl->Pn = Pn;
+    pl->nn = nn;
+    pl->n_sys = n_sys;
+    pl->points = R.points;
+    pl->rho_out = rho_out;
+    pl->e_out = e_out;
+    pl->own_scratch = !borrow_scratch;
+    std::memset(&pl->P, 0, sizeof(pl->P));
+    auto fail = [&](md_status s) {
+        plan_free(pl);
+        return s;
+    };
+#define PTRY(expr)                                                                          \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess)                                                              \
+            return fail(set_error((_e == cudaErrorMemoryAllocation) ? MD_ERR_OOM : MD_ERR_CUDA, \
+                                  std::string("CUDA: ") + cudaGetErrorString(_e) + " (" #expr ")")); \
+    } while (0)
+    PTRY(cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking));
+    PTRY(cudaEventCreate(&pl->ev0));
+    PTRY(cudaEventCreate(&pl->ev1));
+    if (n_sys == 0) {
+        *out = pl;
         return MD_OK;
     }
-    if (n_sys > (1LL << 31) - 1) return set_error(MD_ERR_INVALID, "too many systems");
-    MD_TRY_CUDA(cudaGetDevice(&dev));
-    MD_TRY_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    int dev = 0, n_sm = 0;
+    PTRY(cudaGetDevice(&dev));
+    PTRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
 
-    // scheduling order: big regions first, then poles nearest the real axis
-    sys.resize(n_sys);
+    // cost-sorted work list: big regions first, then poles nearest the real axis
+    std::vector<SysDesc> sys(n_sys);
     for (long long j = 0; j < nn; ++j)
         for (int p = 0; p < Pn; ++p) sys[j * Pn + p] = SysDesc{(int)j, p};
     std::stable_sort(sys.begin(), sys.end(), [&](const SysDesc& a, const SysDesc& b) {
@@ -234,40 +403,30 @@ md_status run_solver(Ham& H, const md_poles* poles, const Regions& R, const md_s
         const double cb = (double)R.points[b.node] / std::sqrt(poles->z[2 * b.pole + 1]);
         return ca > cb;
     });
+    PTRY(cudaMalloc(&pl->d_sys, n_sys * sizeof(SysDesc)));
+    PTRY(cudaMalloc(&pl->d_nodes, nn * sizeof(NodeDesc)));
+    PTRY(cudaMalloc(&pl->d_status, n_sys * sizeof(int)));
+    PTRY(cudaMalloc(&pl->d_iters, n_sys * sizeof(int)));
+    PTRY(cudaMalloc(&pl->d_nrel, n_sys * sizeof(int)));
+    PTRY(cudaMalloc(&pl->d_resid, n_sys * sizeof(double)));
+    PTRY(cudaMalloc(&pl->d_xsrc, n_sys * sizeof(double2)));
+    PTRY(cudaMalloc(&pl->d_z, Pn * sizeof(double2)));
+    PTRY(cudaMalloc(&pl->d_w, Pn * sizeof(double2)));
+    PTRY(cudaMalloc(&pl->d_counter, sizeof(unsigned int)));
+    PTRY(cudaMemcpy(pl->d_sys, sys.data(), n_sys * sizeof(SysDesc), cudaMemcpyHostToDevice));
+    PTRY(cudaMemcpy(pl->d_nodes, R.desc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice));
+    PTRY(cudaMemcpy(pl->d_z, poles->z, Pn * sizeof(double2), cudaMemcpyHostToDevice));
+    PTRY(cudaMemcpy(pl->d_w, poles->w, Pn * sizeof(double2), cudaMemcpyHostToDevice));
+    PTRY(cudaMemset(pl->d_iters, 0, n_sys * sizeof(int)));
     if (ckpt) {
-        ckoff.resize(n_sys);
+        std::vector<long long> ckoff(n_sys);
         for (long long j = 0; j < nn; ++j)
             for (int p = 0; p < Pn; ++p) ckoff[j * Pn + p] = Pn * ckpt->node_off[j] + p * R.points[j];
+        PTRY(cudaMalloc(&pl->d_ckoff, n_sys * sizeof(long long)));
+        PTRY(cudaMemcpy(pl->d_ckoff, ckoff.data(), n_sys * sizeof(long long), cudaMemcpyHostToDevice));
     }
 
-    block = opts.block > 0 ? opts.block : 512;
-    per_sm = opts.ctas_per_sm > 0 ? opts.ctas_per_sm : std::max(1, 1024 / block);
-    grid = (int)std::min<long long>((long long)n_sm * per_sm, n_sys);
-    n_max_r = (R.n_max + 63) / 64 * 64;
-    slot = slot_bytes_for(opts.precision, R.n_max);
-    need = slot * (size_t)grid;
-    if (need > H.scratch_bytes) {
-        if (H.scratch) cudaFree(H.scratch);
-        H.scratch = nullptr;
-        H.scratch_bytes = 0;
-        MD_TRY_CUDA(cudaMalloc(&H.scratch, need));
-        H.scratch_bytes = need;
-    }
-    MD_TRY_CUDA(cudaMallocAsync((void**)&d_sys, n_sys * sizeof(SysDesc), stream));
-    MD_TRY_CUDA(cudaMallocAsync((void**)&d_nodes, nn * sizeof(NodeDesc), stream));
-    MD_TRY_CUDA(cudaMallocAsync((void**)&d_status, n_sys * sizeof(int), stream));
-    MD_TRY_CUDA(cudaMallocAsync((void**)&d_iters, n_sys * sizeof(int), stream));
-    MD_TRY_CUDA(cudaMallocAsync((void**)&d_nrel, n_sys * sizeof(int), stream));
-    MD_TRY_CUDA(cudaMallocAsync((void**)&d_resid, n_sys * sizeof(double), stream));
-    MD_TRY_CUDA(cudaMallocAsync((void**)&d_counter, sizeof(unsigned int), stream));
-    MD_TRY_CUDA(cudaMemcpyAsync(d_sys, sys.data(), n_sys * sizeof(SysDesc), cudaMemcpyHostToDevice, stream));
-    MD_TRY_CUDA(cudaMemcpyAsync(d_nodes, R.desc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, stream));
-    MD_TRY_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream));
-    if (ckpt) {
-        MD_TRY_CUDA(cudaMallocAsync((void**)&d_ckoff, n_sys * sizeof(long long), stream));
-        MD_TRY_CUDA(cudaMemcpyAsync(d_ckoff, ckoff.data(), n_sys * sizeof(long long), cudaMemcpyHostToDevice, stream));
-    }
-
+    SolveParams& P = pl->P;
     for (int d = 0; d < 3; ++d) {
         P.n[d] = H.n[d];
         P.periodic[d] = H.periodic[d];
@@ -298,136 +457,141 @@ md_status run_solver(Ham& H, const md_poles* poles, const Regions& R, const md_s
     P.e_p = H.e_p;
     P.n_sys = (int)n_sys;
     P.P = Pn;
-    P.sys = d_sys;
-    P.nodes = d_nodes;
-    P.z = d_z;
+    P.sys = pl->d_sys;
+    P.nodes = pl->d_nodes;
+    P.z = pl->d_z;
     P.tol = opts.tol;
     P.maxit = opts.maxit;
     P.reliable_every = opts.reliable_every;
     P.reliable_delta = opts.reliable_delta;
     P.timeout_ns = opts.timeout_s > 0 ? (unsigned long long)(opts.timeout_s * 1e9) : 0ULL;
-    P.scratch = (char*)H.scratch;
-    P.slot_bytes = slot;
-    P.n_max = (int)n_max_r;
+    P.slot_bytes = slot_bytes_for(opts.precision, R.n_max);
+    P.n_max = (int)((R.n_max + 63) / 64 * 64);
     P.ckpt = ckpt ? (double2*)ckpt->x : nullptr;
-    P.ckpt_sys_off = d_ckoff;
-    P.work_counter = d_counter;
-    P.x_src = d_xsrc;
-    P.status = d_status;
-    P.iters = d_iters;
-    P.resid = d_resid;
-    P.n_rel = d_nrel;
+    P.ckpt_sys_off = pl->d_ckoff;
+    P.work_counter = pl->d_counter;
+    P.x_src = pl->d_xsrc;
+    P.status = pl->d_status;
+    P.iters = pl->d_iters;
+    P.resid = pl->d_resid;
+    P.n_rel = pl->d_nrel;
 
-    MD_TRY_CUDA(cudaEventCreate(&ev0));
-    MD_TRY_CUDA(cudaEventCreate(&ev1));
-    MD_TRY_CUDA(cudaEventRecord(ev0, stream));
-    MD_TRY_CUDA(launch_cocg(P, opts.precision, grid, block, stream));
-    MD_TRY_CUDA(cudaEventRecord(ev1, stream));
-
-    h_status.resize(n_sys);
-    h_iters.resize(n_sys);
-    h_nrel.resize(n_sys);
-    h_resid.resize(n_sys);
-    MD_TRY_CUDA(cudaMemcpyAsync(h_status.data(), d_status, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream));
-    MD_TRY_CUDA(cudaMemcpyAsync(h_iters.data(), d_iters, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream));
-    MD_TRY_CUDA(cudaMemcpyAsync(h_nrel.data(), d_nrel, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream));
-    MD_TRY_CUDA(cudaMemcpyAsync(h_resid.data(), d_resid, n_sys * sizeof(double), cudaMemcpyDeviceToHost, stream));
-    MD_TRY_CUDA(cudaStreamSynchronize(stream));
-    MD_TRY_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
-    {
-        md_stats sst;
-        std::memset(&sst, 0, sizeof(sst));
-        sst.n_systems = n_sys;
-        sst.iters_min = 1 << 30;
-        for (long long k = 0; k < n_sys; ++k) {
-            const int s = h_status[k];
-            if (s == 0) sst.n_converged++;
-            else if (s == 2) sst.n_noconv++;
-            else if (s == 3) sst.n_breakdown++;
-            else if (s == 4) sst.n_timeout++;
-            sst.iters_min = std::min(sst.iters_min, h_iters[k]);
-            sst.iters_max = std::max(sst.iters_max, h_iters[k]);
-            sst.total_iters += h_iters[k];
-            sst.total_point_iters += (long long)h_iters[k] * R.points[k / Pn];
-            sst.reliable_updates += h_nrel[k];
-            sst.max_resid = std::max(sst.max_resid, h_resid[k]);
+    // scratch sized for the largest launch shape (4 CTAs of 256 per SM)
+    const int max_ctas = (int)std::min<long long>((long long)n_sm * 4, n_sys);
+    const size_t need = P.slot_bytes * (size_t)max_ctas;
+    if (borrow_scratch) {
+        if (need > H.scratch_bytes) {
+            if (H.scratch) cudaFree(H.scratch);
+            H.scratch = nullptr;
+            H.scratch_bytes = 0;
+            PTRY(cudaMalloc(&H.scratch, need));
+            H.scratch_bytes = need;
         }
-        sst.iters_mean = (double)sst.total_iters / (double)n_sys;
-        sst.kernel_ms = ms;
-        if (stats) *stats = sst;
-        bool invalid = false;
-        for (long long k = 0; k < n_sys; ++k) invalid = invalid || h_status[k] == 1;
-        if (invalid) {
-            st = set_error(MD_ERR_INVALID, "a region meets more projector atoms than the solver holds (256)");
-        } else if (sst.n_timeout) {
-            st = set_error(MD_ERR_TIMEOUT, "device time budget exhausted; outputs incomplete");
-        } else if (sst.n_breakdown) {
-            st = set_error(MD_ERR_BREAKDOWN, "COCG breakdown (r^T r ~ 0) in some systems");
-        } else if (sst.n_noconv) {
-            st = set_error(MD_ERR_NOCONV, "some systems reached maxit");
-        }
+        pl->scratch = H.scratch;
+    } else {
+        PTRY(cudaMalloc(&pl->scratch, need));
     }
-done:
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
-    cudaFreeAsync(d_sys, stream);
-    cudaFreeAsync(d_nodes, stream);
-    cudaFreeAsync(d_status, stream);
-    cudaFreeAsync(d_iters, stream);
-    cudaFreeAsync(d_nrel, stream);
-    cudaFreeAsync(d_resid, stream);
-    cudaFreeAsync(d_counter, stream);
-    if (d_ckoff) cudaFreeAsync(d_ckoff, stream);
-    return st;
+    P.scratch = (char*)pl->scratch;
+    pl->grid = max_ctas;
+
+    int block = opts.block, per_sm = opts.ctas_per_sm;
+    if (block <= 0) {
+        md_status ts = autotune(pl, n_sm, block, per_sm);
+        if (ts != MD_OK) return fail(ts);
+    }
+    if (per_sm <= 0) per_sm = std::max(1, 1024 / block);
+    per_sm = std::min(per_sm, 4);
+    pl->block = block;
+    pl->grid = (int)std::min<long long>((long long)n_sm * per_sm, n_sys);
+
+    // capture [reset counter, solver, accumulation] once; launches replay it
+    PTRY(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
+    {
+        cudaError_t e1 = cudaMemsetAsync(pl->d_counter, 0, sizeof(unsigned int), pl->cap);
+        cudaError_t e2 = launch_cocg(P, pl->precision, pl->grid, pl->block, pl->cap);
+        cudaError_t e3 = launch_accumulate((int)nn, Pn, pl->d_xsrc, pl->d_z, pl->d_w, H.dV, rho_out, e_out, pl->cap);
+        cudaError_t e4 = cudaStreamEndCapture(pl->cap, &pl->graph);
+        PTRY(e1);
+        PTRY(e2);
+        PTRY(e3);
+        PTRY(e4);
+    }
+    PTRY(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+#undef PTRY
+    *out = pl;
+    return MD_OK;
 }
 
-md_status upload_poles(const md_poles* poles, double2** d_z, double2** d_w, cudaStream_t stream) {
-    const int Pn = poles->n_poles;
-    cudaError_t e = cudaMallocAsync((void**)d_z, Pn * sizeof(double2), stream);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)d_w, Pn * sizeof(double2), stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(*d_z, poles->z, Pn * sizeof(double2), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(*d_w, poles->w, Pn * sizeof(double2), cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+md_status plan_launch(md_plan* pl, cudaStream_t stream) {
+    if (!pl) return set_error(MD_ERR_INVALID, "plan is NULL");
+    if (pl->n_sys == 0) return MD_OK;
+    PLAN_TRY(cudaEventRecord(pl->ev0, stream));
+    PLAN_TRY(cudaGraphLaunch(pl->exec, stream));
+    PLAN_TRY(cudaEventRecord(pl->ev1, stream));
+    pl->launched = true;
+    return MD_OK;
+}
+
+md_status plan_stats(md_plan* pl, cudaStream_t stream, md_stats* stats) {
+    if (!pl) return set_error(MD_ERR_INVALID, "plan is NULL");
+    md_stats sst;
+    std::memset(&sst, 0, sizeof(sst));
+    if (pl->n_sys == 0 || !pl->launched) {
+        if (stats) *stats = sst;
+        return MD_OK;
+    }
+    const long long n_sys = pl->n_sys;
+    std::vector<int> h_status(n_sys), h_iters(n_sys), h_nrel(n_sys);
+    std::vector<double> h_resid(n_sys);
+    PLAN_TRY(cudaMemcpyAsync(h_status.data(), pl->d_status, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    PLAN_TRY(cudaMemcpyAsync(h_iters.data(), pl->d_iters, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    PLAN_TRY(cudaMemcpyAsync(h_nrel.data(), pl->d_nrel, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    PLAN_TRY(cudaMemcpyAsync(h_resid.data(), pl->d_resid, n_sys * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    PLAN_TRY(cudaStreamSynchronize(stream));
+    float ms = 0.f;
+    PLAN_TRY(cudaEventElapsedTime(&ms, pl->ev0, pl->ev1));
+    sst.n_systems = n_sys;
+    sst.iters_min = 1 << 30;
+    bool invalid = false;
+    for (long long k = 0; k < n_sys; ++k) {
+        const int s = h_status[k];
+        if (s == 0) sst.n_converged++;
+        else if (s == 2) sst.n_noconv++;
+        else if (s == 3) sst.n_breakdown++;
+        else if (s == 4) sst.n_timeout++;
+        else if (s == 1) invalid = true;
+        sst.iters_min = std::min(sst.iters_min, h_iters[k]);
+        sst.iters_max = std::max(sst.iters_max, h_iters[k]);
+        sst.total_iters += h_iters[k];
+        sst.total_point_iters += (long long)h_iters[k] * pl->points[k / pl->Pn];
+        sst.reliable_updates += h_nrel[k];
+        sst.max_resid = std::max(sst.max_resid, h_resid[k]);
+    }
+    sst.iters_mean = (double)sst.total_iters / (double)n_sys;
+    sst.kernel_ms = ms;
+    if (stats) *stats = sst;
+    if (invalid)
+        return set_error(MD_ERR_INVALID, "a region meets more projector atoms than the solver holds (256)");
+    if (sst.n_timeout) return set_error(MD_ERR_TIMEOUT, "device time budget exhausted; outputs incomplete");
+    if (sst.n_breakdown) return set_error(MD_ERR_BREAKDOWN, "COCG breakdown (r^T r ~ 0) in some systems");
+    if (sst.n_noconv) return set_error(MD_ERR_NOCONV, "some systems reached maxit");
     return MD_OK;
 }
 
 md_status density_impl(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,
                        const md_solver_opts* opts, double* rho_out, double* e_out, md_workspace* ckpt,
                        md_stats* stats, cudaStream_t stream) {
-    md_status st = check_device();
+    md_plan* pl = nullptr;
+    md_status st = plan_create(ham, poles, nodes, opts, rho_out, e_out, ckpt, true, stream, &pl);
     if (st != MD_OK) return st;
-    if (!ham) return set_error(MD_ERR_INVALID, "ham is NULL");
-    if ((st = check_poles(poles)) != MD_OK) return st;
-    if ((st = check_opts(opts)) != MD_OK) return st;
-    Ham& H = const_cast<md_hamiltonian*>(ham)->h;
-    Regions R;
-    if ((st = make_regions(H, nodes, R)) != MD_OK) return st;
-    if (!rho_out && R.desc.size() > 0) return set_error(MD_ERR_INVALID, "rho_out is NULL");
-    if (ckpt) {
-        if (ckpt->n_nodes != (long long)R.desc.size() || ckpt->n_poles != poles->n_poles ||
-            ckpt->total_points != R.total)
-            return set_error(MD_ERR_INVALID, "checkpoint workspace was made for other nodes or poles");
-    }
-    const long long nn = (long long)R.desc.size();
-    if (nn == 0) {
+    if (pl->n_sys == 0) {
         if (stats) std::memset(stats, 0, sizeof(*stats));
+        plan_free(pl);
         return MD_OK;
     }
-    double2* d_z = nullptr;
-    double2* d_w = nullptr;
-    double2* d_xsrc = nullptr;
-    md_status st2 = MD_OK;
-    if ((st = upload_poles(poles, &d_z, &d_w, stream)) != MD_OK) goto done;
-    MD_TRY_CUDA(cudaMallocAsync((void**)&d_xsrc, nn * poles->n_poles * sizeof(double2), stream));
-    st2 = run_solver(H, poles, R, opts, d_xsrc, ckpt, stats, stream, d_z);
-    if (st2 == MD_OK || st2 == MD_ERR_NOCONV || st2 == MD_ERR_BREAKDOWN || st2 == MD_ERR_TIMEOUT) {
-        MD_TRY_CUDA(launch_accumulate((int)nn, poles->n_poles, d_xsrc, d_z, d_w, H.dV, rho_out, e_out, stream));
-    }
-    st = st2;
-done:
-    cudaFreeAsync(d_z, stream);
-    cudaFreeAsync(d_w, stream);
-    cudaFreeAsync(d_xsrc, stream);
+    st = plan_launch(pl, stream);
+    if (st == MD_OK) st = plan_stats(pl, stream, stats);
+    plan_free(pl);
     return st;
 }
 
@@ -733,6 +897,38 @@ done:
         md_workspace_destroy(own);
     }
     return st;
+}
+
+md_status md_plan_create(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,
+                         const md_solver_opts* opts, double* rho_out, double* e_out, md_workspace* ckpt,
+                         void* stream, md_plan** out) {
+    clear_error();
+    if (!out) return set_error(MD_ERR_INVALID, "out is NULL");
+    return plan_create(ham, poles, nodes, opts, rho_out, e_out, ckpt, false, (cudaStream_t)stream, out);
+}
+
+md_status md_plan_launch(md_plan* plan, void* stream) {
+    clear_error();
+    return plan_launch(plan, (cudaStream_t)stream);
+}
+
+md_status md_plan_stats(md_plan* plan, void* stream, md_stats* stats) {
+    clear_error();
+    return plan_stats(plan, (cudaStream_t)stream, stats);
+}
+
+md_status md_plan_launch_shape(const md_plan* plan, int32_t* block, int32_t* grid) {
+    clear_error();
+    if (!plan || !block || !grid) return set_error(MD_ERR_INVALID, "plan, block and grid are required");
+    *block = plan->block;
+    *grid = plan->grid;
+    return MD_OK;
+}
+
+md_status md_plan_destroy(md_plan* plan) {
+    clear_error();
+    plan_free(plan);
+    return MD_OK;
 }
 
 md_status md_hamiltonian_set_potential(md_hamiltonian* ham, const double* V_in, void* stream) {

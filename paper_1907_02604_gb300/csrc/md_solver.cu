@@ -50,6 +50,29 @@ constexpr int kMapMax = 4096;   // direct global->local atom map when n_atoms <=
 constexpr int kChunk = 8;       // points per FP32 partial sum before it joins the FP64 sum
 constexpr int kStop = 1, kRefresh = 2, kStopTimeout = 3;
 
+// Per-thread partial sum: compensated (Kahan) in float, plain in double.
+// The float partial is rounded to double once, where the block reduction
+// (double) takes over.
+template <class R>
+struct KSum;
+template <>
+struct KSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+template <>
+struct KSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+
 struct FastDiv {
     uint32_t m;
     uint32_t l;
@@ -100,6 +123,10 @@ struct Shared {
     float coefF[3][kMaxQ];
     double alpha[2];
     double beta[2];
+    // COCG scalar state, owned by thread 0
+    double rho[2];        // r^T r
+    double rn, rn_last;   // ||r||, ||r|| at the last residual refresh
+    int it, last_rel, n_rel, st;
     int action;
     int status;
     int sys;
@@ -438,6 +465,43 @@ __device__ __forceinline__ C matvec_point(const SolveParams& P, const Geo& G, co
     return cmake<C>(yx, yy);
 }
 
+// Mixed mode: flush dx into x_hi, then r = e_j - (H_R - z) x_hi in FP64
+// (a reliable update).  Rare, so kept out of line to spare registers in the
+// iteration.  On return thread 0 holds r^T r (re, im) and ||r||^2 in t3.
+template <class Mode, int Q>
+__device__ __noinline__ void refresh_residual(const SolveParams& P, const Geo& G, Shared& S,
+                                              typename Mode::cplx* r, typename Mode::cplx* dx,
+                                              double2* x, double2 zd, double (&t3)[3]) {
+    using R = typename Mode::real;
+    using C = typename Mode::cplx;
+    for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
+        const C d = dx[i];
+        double2 xv = x[i];
+        xv.x += (double)d.x;
+        xv.y += (double)d.y;
+        x[i] = xv;
+        dx[i] = cmake<C>((R)0, (R)0);
+    }
+    __syncthreads();
+    if (P.nonlocal) nonlocal_coeffs<double, double2>(P, G, S, x);
+    KSum<R> q_re, q_im;
+    double nrm = 0.0;
+    for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
+        const double2 y = matvec_point<double, double2, Q, double2>(P, G, S, x, i, zd.x, zd.y, P.diag);
+        const double tre = (i == G.src ? 1.0 : 0.0) - y.x;
+        const double tim = -y.y;
+        const C rr = cmake<C>((R)tre, (R)tim);
+        r[i] = rr;
+        q_re.add(rr.x * rr.x - rr.y * rr.y);
+        q_im.add(2 * rr.x * rr.y);
+        nrm += tre * tre + tim * tim;
+    }
+    t3[0] = q_re.get();
+    t3[1] = q_im.get();
+    t3[2] = nrm;
+    block_reduce<3>(S, t3);
+}
+
 template <class Mode, int Q>
 __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolveParams P) {
     using R = typename Mode::real;
@@ -498,173 +562,183 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
         __syncthreads();
 
         // Scalar state lives in thread 0; the others see it through S.
-        double rho_re = 1.0, rho_im = 0.0;   // r^T r
-        double rn = 1.0, rn_last_rel = 1.0;
-        int it = 0, last_rel = 0, n_rel = 0;
-        int status = 2;  // not converged
         if (threadIdx.x == 0) {
             S.beta[0] = 0.0;
             S.beta[1] = 0.0;
             S.action = 0;
+            S.rho[0] = 1.0;
+            S.rho[1] = 0.0;
+            S.rn = 1.0;
+            S.rn_last = 1.0;
+            S.it = 0;
+            S.last_rel = 0;
+            S.n_rel = 0;
+            S.st = 2;   // not converged
         }
         __syncthreads();
 
         for (;;) {
             if (P.timeout_ns && threadIdx.x == 0 && (global_time_ns() - t_start) > P.timeout_ns)
                 S.action = kStopTimeout;
-            if (threadIdx.x == 0 && it >= P.maxit) S.action = kStop;
+            if (threadIdx.x == 0 && S.it >= P.maxit) S.action = kStop;
             __syncthreads();
             if (S.action == kStop || S.action == kStopTimeout) break;
             {   // P1: p = r + beta p
                 const R br = (R)S.beta[0], bi = (R)S.beta[1];
-                for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
-                    const C ri = r[i], pi = p[i];
-                    p[i] = cmake<C>(ri.x + br * pi.x - bi * pi.y, ri.y + br * pi.y + bi * pi.x);
+                if constexpr (Mode::kMixed) {
+                    // two complex64 per 16-byte access (slots are 512-byte aligned)
+                    const float4* r4 = reinterpret_cast<const float4*>(r);
+                    float4* p4 = reinterpret_cast<float4*>(p);
+                    const int npair = G.n >> 1;
+                    for (int k = threadIdx.x; k < npair; k += blockDim.x) {
+                        const float4 a = r4[k], b = p4[k];
+                        p4[k] = make_float4(a.x + br * b.x - bi * b.y, a.y + br * b.y + bi * b.x,
+                                            a.z + br * b.z - bi * b.w, a.w + br * b.w + bi * b.z);
+                    }
+                    if ((G.n & 1) && threadIdx.x == 0) {
+                        const int i = G.n - 1;
+                        const C ri = r[i], pi = p[i];
+                        p[i] = cmake<C>(ri.x + br * pi.x - bi * pi.y, ri.y + br * pi.y + bi * pi.x);
+                    }
+                } else {
+                    for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
+                        const C ri = r[i], pi = p[i];
+                        p[i] = cmake<C>(ri.x + br * pi.x - bi * pi.y, ri.y + br * pi.y + bi * pi.x);
+                    }
                 }
             }
             __syncthreads();
             if (P.nonlocal) nonlocal_coeffs<R, C>(P, G, S, p);
             {   // P2: Ap = (H_R - z) p ; p^T Ap
-                double pap[2] = {0.0, 0.0};
-                R acc_re = 0, acc_im = 0;
-                int cnt = 0;
+                KSum<R> acc_re, acc_im;
                 for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
                     const C y = matvec_point<R, C, Q, C>(P, G, S, p, i, zr, zi, diagR);
                     Ap[i] = y;
                     const C pi = p[i];
-                    acc_re += pi.x * y.x - pi.y * y.y;
-                    acc_im += pi.x * y.y + pi.y * y.x;
-                    if (++cnt == kChunk) {   // short FP32 runs, FP64 above them
-                        pap[0] += (double)acc_re;
-                        pap[1] += (double)acc_im;
-                        acc_re = acc_im = 0;
-                        cnt = 0;
-                    }
+                    acc_re.add(pi.x * y.x - pi.y * y.y);
+                    acc_im.add(pi.x * y.y + pi.y * y.x);
                 }
-                pap[0] += (double)acc_re;
-                pap[1] += (double)acc_im;
+                double pap[2] = {acc_re.get(), acc_im.get()};
                 block_reduce<2>(S, pap);
                 if (threadIdx.x == 0) {
-                    ++it;
+                    ++S.it;
                     const double den = pap[0] * pap[0] + pap[1] * pap[1];
                     if (!(den > 0.0)) {
-                        status = 3;
+                        S.st = 3;
                         S.action = kStop;
                     } else {
-                        S.alpha[0] = (rho_re * pap[0] + rho_im * pap[1]) / den;
-                        S.alpha[1] = (rho_im * pap[0] - rho_re * pap[1]) / den;
+                        S.alpha[0] = (S.rho[0] * pap[0] + S.rho[1] * pap[1]) / den;
+                        S.alpha[1] = (S.rho[1] * pap[0] - S.rho[0] * pap[1]) / den;
                     }
                 }
                 __syncthreads();
                 if (S.action == kStop) break;
             }
-            double red3[3] = {0.0, 0.0, 0.0};
+            double red3[3];
             {   // P3: x += alpha p ; r -= alpha Ap ; r^T r ; |r|^2
                 const double al_re = S.alpha[0], al_im = S.alpha[1];
                 const R ar = (R)al_re, ai = (R)al_im;
-                R s_re = 0, s_im = 0, s_n = 0;
-                int cnt = 0;
-                for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
-                    const C pi = p[i], api = Ap[i];
-                    if (Mode::kMixed) {
-                        C d = dx[i];
+                KSum<R> s_re, s_im, s_n;
+                if constexpr (Mode::kMixed) {
+                    const float4* p4 = reinterpret_cast<const float4*>(p);
+                    const float4* q4 = reinterpret_cast<const float4*>(Ap);
+                    float4* d4 = reinterpret_cast<float4*>(dx);
+                    float4* r4 = reinterpret_cast<float4*>(r);
+                    const int npair = G.n >> 1;
+                    for (int k = threadIdx.x; k < npair; k += blockDim.x) {
+                        const float4 pv = p4[k], qv = q4[k];
+                        float4 d = d4[k], rv = r4[k];
+                        d.x += ar * pv.x - ai * pv.y;
+                        d.y += ar * pv.y + ai * pv.x;
+                        d.z += ar * pv.z - ai * pv.w;
+                        d.w += ar * pv.w + ai * pv.z;
+                        rv.x -= ar * qv.x - ai * qv.y;
+                        rv.y -= ar * qv.y + ai * qv.x;
+                        rv.z -= ar * qv.z - ai * qv.w;
+                        rv.w -= ar * qv.w + ai * qv.z;
+                        d4[k] = d;
+                        r4[k] = rv;
+                        s_re.add(rv.x * rv.x - rv.y * rv.y + (rv.z * rv.z - rv.w * rv.w));
+                        s_im.add(2.f * (rv.x * rv.y + rv.z * rv.w));
+                        s_n.add(rv.x * rv.x + rv.y * rv.y + (rv.z * rv.z + rv.w * rv.w));
+                    }
+                    if ((G.n & 1) && threadIdx.x == 0) {
+                        const int i = G.n - 1;
+                        const C pi = p[i], api = Ap[i];
+                        C d = dx[i], ri = r[i];
                         d.x += ar * pi.x - ai * pi.y;
                         d.y += ar * pi.y + ai * pi.x;
+                        ri.x -= ar * api.x - ai * api.y;
+                        ri.y -= ar * api.y + ai * api.x;
                         dx[i] = d;
-                    } else {
+                        r[i] = ri;
+                        s_re.add(ri.x * ri.x - ri.y * ri.y);
+                        s_im.add(2.f * ri.x * ri.y);
+                        s_n.add(ri.x * ri.x + ri.y * ri.y);
+                    }
+                } else {
+                    for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
+                        const C pi = p[i], api = Ap[i];
                         double2 xv = x[i];
                         xv.x += al_re * (double)pi.x - al_im * (double)pi.y;
                         xv.y += al_re * (double)pi.y + al_im * (double)pi.x;
                         x[i] = xv;
-                    }
-                    C ri = r[i];
-                    ri.x -= ar * api.x - ai * api.y;
-                    ri.y -= ar * api.y + ai * api.x;
-                    r[i] = ri;
-                    s_re += ri.x * ri.x - ri.y * ri.y;
-                    s_im += 2 * ri.x * ri.y;
-                    s_n += ri.x * ri.x + ri.y * ri.y;
-                    if (++cnt == kChunk) {
-                        red3[0] += (double)s_re;
-                        red3[1] += (double)s_im;
-                        red3[2] += (double)s_n;
-                        s_re = s_im = s_n = 0;
-                        cnt = 0;
+                        C ri = r[i];
+                        ri.x -= ar * api.x - ai * api.y;
+                        ri.y -= ar * api.y + ai * api.x;
+                        r[i] = ri;
+                        s_re.add(ri.x * ri.x - ri.y * ri.y);
+                        s_im.add(2 * ri.x * ri.y);
+                        s_n.add(ri.x * ri.x + ri.y * ri.y);
                     }
                 }
-                red3[0] += (double)s_re;
-                red3[1] += (double)s_im;
-                red3[2] += (double)s_n;
+                red3[0] = s_re.get();
+                red3[1] = s_im.get();
+                red3[2] = s_n.get();
                 block_reduce<3>(S, red3);
             }
             if (Mode::kMixed) {
                 if (threadIdx.x == 0) {
-                    rn = sqrt(red3[2]);
-                    const bool want = (rn <= P.tol) || (it - last_rel >= P.reliable_every) ||
-                                      (rn < P.reliable_delta * rn_last_rel);
+                    const double rn = sqrt(red3[2]);
+                    const bool want = (rn <= P.tol) || (S.it - S.last_rel >= P.reliable_every) ||
+                                      (rn < P.reliable_delta * S.rn_last);
                     S.action = want ? kRefresh : 0;
                 }
                 __syncthreads();
                 if (S.action == kRefresh) {
-                    // flush dx into x_hi, then r = e_j - (H_R - z) x_hi in FP64
-                    for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
-                        const C d = dx[i];
-                        double2 xv = x[i];
-                        xv.x += (double)d.x;
-                        xv.y += (double)d.y;
-                        x[i] = xv;
-                        dx[i] = cmake<C>((R)0, (R)0);
-                    }
-                    __syncthreads();
-                    if (P.nonlocal) nonlocal_coeffs<double, double2>(P, G, S, x);
-                    double t3[3] = {0, 0, 0};
-                    for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
-                        const double2 y =
-                            matvec_point<double, double2, Q, double2>(P, G, S, x, i, zd.x, zd.y, P.diag);
-                        const double tre = (i == G.src ? 1.0 : 0.0) - y.x;
-                        const double tim = -y.y;
-                        const C rr = cmake<C>((R)tre, (R)tim);
-                        r[i] = rr;
-                        t3[0] += (double)(rr.x * rr.x - rr.y * rr.y);
-                        t3[1] += (double)(2 * rr.x * rr.y);
-                        t3[2] += tre * tre + tim * tim;
-                    }
-                    block_reduce<3>(S, t3);
+                    refresh_residual<Mode, Q>(P, G, S, r, dx, x, zd, red3);
                     if (threadIdx.x == 0) {
-                        red3[0] = t3[0];
-                        red3[1] = t3[1];
-                        red3[2] = t3[2];
-                        rn_last_rel = sqrt(t3[2]);
-                        last_rel = it;
-                        ++n_rel;
+                        S.rn_last = sqrt(red3[2]);
+                        S.last_rel = S.it;
+                        ++S.n_rel;
                     }
                 }
             }
             if (threadIdx.x == 0) {
-                rn = sqrt(red3[2]);
+                const double rn = sqrt(red3[2]);
+                S.rn = rn;
                 S.action = 0;
                 const double rr_abs = sqrt(red3[0] * red3[0] + red3[1] * red3[1]);
                 if (rn <= P.tol) {
-                    status = 0;
+                    S.st = 0;
                     S.action = kStop;
                 } else if (!(rr_abs > 1e-300) || rr_abs < 1e-14 * rn * rn) {
-                    status = 3;
+                    S.st = 3;
                     S.action = kStop;
                 } else {
-                    const double rd = rho_re * rho_re + rho_im * rho_im;
-                    S.beta[0] = (red3[0] * rho_re + red3[1] * rho_im) / rd;
-                    S.beta[1] = (red3[1] * rho_re - red3[0] * rho_im) / rd;
-                    rho_re = red3[0];
-                    rho_im = red3[1];
+                    const double rd = S.rho[0] * S.rho[0] + S.rho[1] * S.rho[1];
+                    S.beta[0] = (red3[0] * S.rho[0] + red3[1] * S.rho[1]) / rd;
+                    S.beta[1] = (red3[1] * S.rho[0] - red3[0] * S.rho[1]) / rd;
+                    S.rho[0] = red3[0];
+                    S.rho[1] = red3[1];
                 }
             }
             __syncthreads();
             if (S.action == kStop) break;
         }
         const bool timed_out = (S.action == kStopTimeout);
-        if (threadIdx.x == 0) S.status = status;
         __syncthreads();
-        status = S.status;
+        const int status = S.st;
         if (Mode::kMixed && status != 0) {
             for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
                 const C d = dx[i];
@@ -678,9 +752,9 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
         if (threadIdx.x == 0) {
             P.x_src[out_idx] = x[G.src];
             P.status[out_idx] = timed_out ? 4 : (S.flag ? 1 : status);
-            P.iters[out_idx] = it;
-            P.resid[out_idx] = rn;
-            P.n_rel[out_idx] = n_rel;
+            P.iters[out_idx] = S.it;
+            P.resid[out_idx] = S.rn;
+            P.n_rel[out_idx] = S.n_rel;
         }
         if (P.nonlocal) release_local_atoms(P, S);
         __syncthreads();
