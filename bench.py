@@ -236,7 +236,7 @@ def main():
 
     for i in range(args.warmup):
         plan_of(i).launch(stream)
-        plan_of(i).stats(stream)
+        plan_of(i).stats(stream, strict=False)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -254,7 +254,7 @@ def main():
     el_ms = ev0.elapsed_time(ev1)
     # per-step statistics (a plan replayed in the timed region repeats the
     # same solves, so its last launch stands for each of its launches)
-    stats = [plan_of(args.warmup + i).stats(stream) for i in range(args.steps)]
+    stats = [plan_of(args.warmup + i).stats(stream, strict=False) for i in range(args.steps)]
     if dist:
         t = torch.tensor([el_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -282,7 +282,7 @@ def main():
             hm = Hamiltonian.from_workload(w, stream=stream)
             l2, h2 = hm.spectral_bounds(stream=stream)
             z, wt = make_poles(w.kT, w.mu, l2, h2, w.n_poles)
-            rho, e, st = density(hm, z, wt, nd, hw, opts, energy=True, stream=stream)
+            rho, e, st = density(hm, z, wt, nd, hw, opts, energy=True, stream=stream, strict=False)
             rho_h, e_h = rho.cpu(), e.cpu()
             hm.close()
             h2d = (w.v_ext.nbytes + w.atoms.nbytes + w.depth.nbytes + w.sigma.nbytes

@@ -224,6 +224,12 @@ md_status md_plan_launch(md_plan* plan, void* stream);
 md_status md_plan_stats(md_plan* plan, void* stream, md_stats* stats);
 /* Launch shape chosen for the plan (threads per CTA, CTAs in the grid). */
 md_status md_plan_launch_shape(const md_plan* plan, int32_t* block, int32_t* grid);
+/* Per-system outcome of the last launch, indexed node * P + pole: status
+ * (0 converged, 1 too many projector atoms, 2 maxit, 3 breakdown,
+ * 4 deadline), iterations and final residual norm.  Host arrays of
+ * n_nodes * P entries; synchronises `stream`. */
+md_status md_plan_system_info(md_plan* plan, void* stream, int32_t* status, int32_t* iters,
+                              double* resid);
 md_status md_plan_destroy(md_plan* plan);
 
 /* Adjoint of (rho, e) -> L.  With a_j = dL/drho_j and b_j = dL/de_j:

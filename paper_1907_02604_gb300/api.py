@@ -228,6 +228,19 @@ class Plan:
         d["status"] = _lib.STATUS_NAMES[status]
         return d
 
+    def system_info(self, stream=None):
+        """Per-system (status, iterations, residual) of the last launch,
+        indexed node * P + pole."""
+        n = self.n_systems
+        st = np.zeros(n, np.int32)
+        it = np.zeros(n, np.int32)
+        rs = np.zeros(n, np.float64)
+        check(load().md_plan_system_info(self._h, _stream_handle(stream),
+                                         st.ctypes.data_as(_lib.c_int32_p),
+                                         it.ctypes.data_as(_lib.c_int32_p),
+                                         rs.ctypes.data_as(_lib.c_double_p)), "md_plan_system_info")
+        return st, it, rs
+
     def launch_shape(self):
         b, g = ctypes.c_int32(), ctypes.c_int32()
         check(load().md_plan_launch_shape(self._h, ctypes.byref(b), ctypes.byref(g)), "md_plan_launch_shape")

@@ -108,6 +108,8 @@ struct Regions {
     std::vector<long long> points;
     long long total = 0;
     long long n_max = 0;
+    int max_dim[3] = {0, 0, 0};
+    bool any_ring = false;
 };
 
 md_status make_regions(const Ham& H, const md_nodes* nodes, Regions& R) {
@@ -146,6 +148,8 @@ md_status make_regions(const Ham& H, const md_nodes* nodes, Regions& R) {
             pts *= d.dims[ax];
         }
         if (pts > (1LL << 30)) return set_error(MD_ERR_INVALID, "region too large");
+        for (int ax = 0; ax < 3; ++ax) R.max_dim[ax] = std::max(R.max_dim[ax], d.dims[ax]);
+        if (d.ring) R.any_ring = true;
         d.src = srcc[0] + d.dims[0] * (srcc[1] + d.dims[1] * srcc[2]);
         R.points[j] = pts;
         R.total += pts;
@@ -209,6 +213,8 @@ struct md_plan {
     long long nn = 0;
     long long n_sys = 0;
     int grid = 0, block = 0;
+    int variant = 0;                   // 0 generic kernel, K > 0: z-march kernel with K columns per thread
+    size_t smem = 0;                   // dynamic shared memory of the z-march kernel
     std::vector<long long> points;     // region points per node
     md::SolveParams P;
     // device buffers owned by the plan
@@ -261,33 +267,59 @@ void plan_free(md_plan* pl) {
     delete pl;
 }
 
-// Launch-shape autotuner: times each candidate (threads per CTA, CTAs per
-// SM) on the same evenly spread sample of systems with a short iteration
-// cap and keeps the one with the most region-point iterations per second.
-// Results are cached per (precision, stencil width, region-size bucket,
-// nonlocal) for the life of the process.
+struct Shape {
+    int variant, block, per_sm;
+};
+
+cudaError_t launch_shape(const md_plan* pl, const SolveParams& P, const Shape& sh, int grid, cudaStream_t s) {
+    if (sh.variant > 0) return launch_cocg_zm(P, sh.variant, grid, sh.block, pl->smem, s);
+    return launch_cocg(P, pl->precision, grid, sh.block, s);
+}
+
+// Candidate launch shapes: the generic kernel at 1024x1 and 512x2, and, when
+// the z-march kernel applies, K = 1..4 columns per thread with the smallest
+// warp-multiple block covering the largest plane, at every CTAs-per-SM
+// count the occupancy calculator allows.
+std::vector<Shape> candidate_shapes(const md_plan* pl, bool zm_ok, int max_plane) {
+    std::vector<Shape> c = {{0, 1024, 1}, {0, 512, 2}};
+    if (!zm_ok) return c;
+    for (int K = 1; K <= 4; ++K) {
+        const int need = (max_plane + K - 1) / K;
+        const int block = (need + 31) / 32 * 32;
+        if (block > zm_max_threads(K) || block < 64) continue;
+        const int occ = zm_occupancy(pl->P.q, K, block, pl->smem);
+        for (int per = 1; per <= std::min(occ, 2); ++per) c.push_back({K, block, per});
+    }
+    return c;
+}
+
+// Launch-shape autotuner: times each candidate on the same evenly spread
+// sample of systems with a short iteration cap and keeps the one with the
+// most region-point iterations per second.  Results are cached per
+// (precision, stencil width, region-size bucket, nonlocal, z-march
+// eligibility) for the life of the process.
 struct TuneKey {
-    int precision, q, bucket, nonlocal;
+    int precision, q, bucket, nonlocal, zm;
     bool operator==(const TuneKey& o) const {
-        return precision == o.precision && q == o.q && bucket == o.bucket && nonlocal == o.nonlocal;
+        return precision == o.precision && q == o.q && bucket == o.bucket && nonlocal == o.nonlocal &&
+               zm == o.zm;
     }
 };
 struct TuneEntry {
     TuneKey key;
-    int block, per_sm;
+    Shape shape;
 };
 std::vector<TuneEntry> g_tune_cache;
 
-md_status autotune(md_plan* pl, int n_sm, int& block_out, int& per_sm_out) {
-    const TuneKey key{pl->precision, pl->P.q, (int)((pl->P.n_max + 8191) / 8192), pl->P.nonlocal};
+md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_t scratch_bytes,
+                   Shape& out) {
+    const TuneKey key{pl->precision, pl->P.q, (int)((pl->P.n_max + 4095) / 4096), pl->P.nonlocal,
+                      cands.size() > 2 ? 1 : 0};
     for (const auto& e : g_tune_cache)
         if (e.key == key) {
-            block_out = e.block;
-            per_sm_out = e.per_sm;
+            out = e.shape;
             return MD_OK;
         }
-    const int cand[][2] = {{1024, 1}, {512, 2}, {768, 1}, {256, 4}, {512, 1}};
-    // sample: up to n_sm systems spread evenly over the cost-sorted list
     const long long ns = std::min<long long>(pl->n_sys, n_sm);
     std::vector<SysDesc> all(pl->n_sys), sample;
     PLAN_TRY(cudaMemcpy(all.data(), pl->d_sys, pl->n_sys * sizeof(SysDesc), cudaMemcpyDeviceToHost));
@@ -296,20 +328,19 @@ md_status autotune(md_plan* pl, int n_sm, int& block_out, int& per_sm_out) {
     PLAN_TRY(cudaMalloc(&d_sample, ns * sizeof(SysDesc)));
     cudaMemcpy(d_sample, sample.data(), ns * sizeof(SysDesc), cudaMemcpyHostToDevice);
     double best = -1.0;
-    int bb = 512, bp = 2;
-    for (const auto& c : cand) {
+    Shape bs = cands[0];
+    std::vector<int> h_it(pl->n_sys);
+    for (const auto& c : cands) {
         SolveParams T = pl->P;
         T.sys = d_sample;
         T.n_sys = (int)ns;
         T.maxit = std::min(pl->P.maxit, 48);
         T.ckpt = nullptr;   // trials never touch the checkpoint
-        const int grid = (int)std::min<long long>((long long)n_sm * c[1], ns);
-        const size_t need = pl->P.slot_bytes * (size_t)grid;
-        size_t have = pl->own_scratch ? pl->P.slot_bytes * (size_t)pl->grid : pl->H->scratch_bytes;
-        if (need > have) continue;
+        const int grid = (int)std::min<long long>((long long)n_sm * c.per_sm, ns);
+        if (pl->P.slot_bytes * (size_t)grid > scratch_bytes) continue;
         cudaMemset(T.work_counter, 0, sizeof(unsigned int));
         cudaEventRecord(pl->ev0, pl->cap);
-        cudaError_t e = launch_cocg(T, pl->precision, grid, c[0], pl->cap);
+        cudaError_t e = launch_shape(pl, T, c, grid, pl->cap);
         cudaEventRecord(pl->ev1, pl->cap);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -321,22 +352,18 @@ md_status autotune(md_plan* pl, int n_sm, int& block_out, int& per_sm_out) {
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, pl->ev0, pl->ev1);
-        // work done: the trial writes iters at indices node*P + pole of the sample
-        long long pit = 0;
-        std::vector<int> h_it(pl->n_sys);
         cudaMemcpy(h_it.data(), T.iters, pl->n_sys * sizeof(int), cudaMemcpyDeviceToHost);
+        long long pit = 0;
         for (const auto& sd : sample) pit += (long long)h_it[(long long)sd.node * pl->Pn + sd.pole] * pl->points[sd.node];
         const double rate = ms > 0 ? (double)pit / ms : 0.0;
         if (rate > best) {
             best = rate;
-            bb = c[0];
-            bp = c[1];
+            bs = c;
         }
     }
     cudaFree(d_sample);
-    g_tune_cache.push_back(TuneEntry{key, bb, bp});
-    block_out = bb;
-    per_sm_out = bp;
+    g_tune_cache.push_back(TuneEntry{key, bs});
+    out = bs;
     return MD_OK;
 }
 
@@ -476,8 +503,11 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     P.resid = pl->d_resid;
     P.n_rel = pl->d_nrel;
 
-    // scratch sized for the largest launch shape (4 CTAs of 256 per SM)
-    const int max_ctas = (int)std::min<long long>((long long)n_sm * 4, n_sys);
+    const int max_plane = R.max_dim[0] * R.max_dim[1];
+    const bool zm_ok = zm_supported(opts.precision, H.q) && !R.any_ring;
+    if (zm_ok) pl->smem = zm_smem_bytes(H.q, R.max_dim[0], R.max_dim[1]);
+    // scratch sized for the widest candidate (2 CTAs per SM)
+    const int max_ctas = (int)std::min<long long>((long long)n_sm * 2, n_sys);
     const size_t need = P.slot_bytes * (size_t)max_ctas;
     if (borrow_scratch) {
         if (need > H.scratch_bytes) {
@@ -492,23 +522,24 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
         PTRY(cudaMalloc(&pl->scratch, need));
     }
     P.scratch = (char*)pl->scratch;
-    pl->grid = max_ctas;
 
-    int block = opts.block, per_sm = opts.ctas_per_sm;
-    if (block <= 0) {
-        md_status ts = autotune(pl, n_sm, block, per_sm);
+    Shape shape{0, opts.block > 0 ? opts.block : 512, opts.ctas_per_sm > 0 ? opts.ctas_per_sm : 0};
+    if (opts.block <= 0) {
+        const std::vector<Shape> cands = candidate_shapes(pl, zm_ok, max_plane);
+        md_status ts = autotune(pl, n_sm, cands, need, shape);
         if (ts != MD_OK) return fail(ts);
     }
-    if (per_sm <= 0) per_sm = std::max(1, 1024 / block);
-    per_sm = std::min(per_sm, 4);
-    pl->block = block;
-    pl->grid = (int)std::min<long long>((long long)n_sm * per_sm, n_sys);
+    if (shape.per_sm <= 0) shape.per_sm = std::max(1, 1024 / shape.block);
+    shape.per_sm = std::min(shape.per_sm, 2);
+    pl->variant = shape.variant;
+    pl->block = shape.block;
+    pl->grid = (int)std::min<long long>((long long)n_sm * shape.per_sm, n_sys);
 
     // capture [reset counter, solver, accumulation] once; launches replay it
     PTRY(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
     {
         cudaError_t e1 = cudaMemsetAsync(pl->d_counter, 0, sizeof(unsigned int), pl->cap);
-        cudaError_t e2 = launch_cocg(P, pl->precision, pl->grid, pl->block, pl->cap);
+        cudaError_t e2 = launch_shape(pl, P, Shape{pl->variant, pl->block, 0}, pl->grid, pl->cap);
         cudaError_t e3 = launch_accumulate((int)nn, Pn, pl->d_xsrc, pl->d_z, pl->d_w, H.dV, rho_out, e_out, pl->cap);
         cudaError_t e4 = cudaStreamEndCapture(pl->cap, &pl->graph);
         PTRY(e1);
@@ -922,6 +953,20 @@ md_status md_plan_launch_shape(const md_plan* plan, int32_t* block, int32_t* gri
     if (!plan || !block || !grid) return set_error(MD_ERR_INVALID, "plan, block and grid are required");
     *block = plan->block;
     *grid = plan->grid;
+    return MD_OK;
+}
+
+md_status md_plan_system_info(md_plan* plan, void* stream, int32_t* status, int32_t* iters,
+                              double* resid) {
+    clear_error();
+    if (!plan || !status || !iters || !resid) return set_error(MD_ERR_INVALID, "plan and outputs are required");
+    if (plan->n_sys == 0) return MD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(status, plan->d_status, plan->n_sys * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(iters, plan->d_iters, plan->n_sys * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(resid, plan->d_resid, plan->n_sys * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
     return MD_OK;
 }
 

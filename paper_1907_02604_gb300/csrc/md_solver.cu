@@ -66,6 +66,12 @@ struct KSum<float> {
     }
     __device__ __forceinline__ double get() const { return (double)s - (double)c; }
 };
+struct MixedModeT {
+    using real = float;
+    using cplx = float2;
+    static constexpr bool kMixed = true;
+};
+
 template <>
 struct KSum<double> {
     double s = 0.0;
@@ -135,6 +141,7 @@ struct Shared {
     int la_id[kLocal];
     short la_off[kLocal][3];
     double2 c[kLocal][4];   // E_l dV C_l sum_i f_l(i) v(i), double
+    double2 pnl[32];        // per warp: sum over its atoms of E_l dV c_l^2 (v^T V_nl v)
     float2 cf[kLocal][4];   // the same rounded to float
     short map[kMapMax];     // global atom id -> local slot, -1 if absent
 };
@@ -300,6 +307,7 @@ __device__ void nonlocal_coeffs(const SolveParams& P, const Geo& G, Shared& S, c
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const R* dt = Tab<R>::d(P);
     const R* gt = Tab<R>::g(P);
+    double pnl_re = 0.0, pnl_im = 0.0, t_re = 0.0, t_im = 0.0;
     for (int k = warp; k < S.n_local; k += nw) {
         const int a = S.la_id[k];
         const int lx = __ldg(P.proj_len + 3 * a), ly = __ldg(P.proj_len + 3 * a + 1),
@@ -353,8 +361,22 @@ __device__ void nonlocal_coeffs(const SolveParams& P, const Geo& G, Shared& S, c
             if (lane == 3) { sr = s[6]; si = s[7]; }
             S.c[k][lane] = make_double2(E * sr, E * si);
             S.cf[k][lane] = make_float2((float)(E * sr), (float)(E * si));
+            // bilinear nonlocal energy of v: E_l dV (C_l s)^2
+            t_re = E * Cl * (sr * sr - si * si);
+            t_im = E * Cl * 2.0 * sr * si;
         }
+        t_re += __shfl_xor_sync(0xffffffffu, t_re, 1);
+        t_im += __shfl_xor_sync(0xffffffffu, t_im, 1);
+        t_re += __shfl_xor_sync(0xffffffffu, t_re, 2);
+        t_im += __shfl_xor_sync(0xffffffffu, t_im, 2);
+        if (lane == 0) {
+            pnl_re += t_re;
+            pnl_im += t_im;
+        }
+        t_re = 0.0;
+        t_im = 0.0;
     }
+    if (lane == 0) S.pnl[warp] = make_double2(pnl_re, pnl_im);
     __syncthreads();
 }
 
@@ -780,16 +802,375 @@ __global__ void k_accumulate(int n_nodes, int Pn, const double2* __restrict__ x_
     if (e) e[j] = 2.0 * se;
 }
 
+
+// Nonlocal part of (H_R v)(i) from the coefficients in S.cf (mixed path).
+__device__ __forceinline__ float2 nl_apply(const SolveParams& P, const Geo& G, const Shared& S, int i) {
+    const int c = (int)fdiv((uint32_t)i, G.div_plane);
+    const int rem = i - c * G.plane;
+    const int b = (int)fdiv((uint32_t)rem, G.div_row);
+    const int a = rem - b * G.m[0];
+    const int gx = wrap_once(G.lo[0] + a, P.n[0]);
+    const int gy = wrap_once(G.lo[1] + b, P.n[1]);
+    const int gz = wrap_once(G.lo[2] + c, P.n[2]);
+    const long long gi = gx + (long long)P.n[0] * (gy + (long long)P.n[1] * gz);
+    float yx = 0.f, yy = 0.f;
+    const int e0 = __ldg(P.pl_ptr + gi), e1 = __ldg(P.pl_ptr + gi + 1);
+    for (int e = e0; e < e1; ++e) {
+        const int k = local_slot(P, S, __ldg(P.pl_atom + e));
+        if (k < 0) continue;
+        const float4 f = __ldg(P.pl_val32 + e);
+        const float2 c0 = S.cf[k][0], c1 = S.cf[k][1], c2 = S.cf[k][2], c3 = S.cf[k][3];
+        yx += f.x * c0.x + f.y * c1.x + f.z * c2.x + f.w * c3.x;
+        yy += f.x * c0.y + f.y * c1.y + f.z * c2.y + f.w * c3.y;
+    }
+    return make_float2(yx, yy);
+}
+
+template <int K>
+struct ZmThreads {
+    static constexpr int value = K == 1 ? 1024 : (K == 2 ? 576 : (K == 3 ? 384 : 288));
+};
+
+// Fused P1 + local P2 of the mixed iteration, staged through shared memory.
+// Each thread owns K (x, y) columns of the region and walks z; the 2Q+1
+// values of p_new along a column sit in registers (the z part of the
+// stencil), and the current plane is published in a zero-bordered buffer
+// of (m0 + 2Q) x (m1 + 2Q) points for the x and y neighbours.  Two buffers
+// alternate, so one barrier per plane suffices.  p_new = r + beta p_old is
+// formed once as a value enters the window and written back to global
+// memory; the next plane's r and p_old and this plane's V are loaded one
+// step ahead.  Outputs: p (new), Ap_loc = (-1/2 L + V - z) p, and the
+// thread's partial of p^T Ap_loc.
+template <int Q, int K>
+__device__ __forceinline__ void zm_stencil_pass(const SolveParams& P, const Geo& G, const Shared& S,
+                                                float2* __restrict__ sbuf, const float2* __restrict__ r,
+                                                float2* __restrict__ p, float2* __restrict__ Ap,
+                                                float br, float bi, float zr, float zi, float diag,
+                                                KSum<float>& acc_re, KSum<float>& acc_im) {
+    const int T = blockDim.x;
+    const int m0 = G.m[0], m1 = G.m[1], m2 = G.m[2], plane = G.plane;
+    const int pitch = m0 + 2 * Q;
+    const int bufsz = pitch * (m1 + 2 * Q);
+    const long long nxy = (long long)P.n[0] * P.n[1];
+    const float* cf = coef_of<float>(S);
+    int col[K], sidx[K];
+    long long vbase[K];
+    bool ok[K];
+    float2 win[K][2 * Q + 1];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        col[k] = threadIdx.x + k * T;
+        ok[k] = col[k] < plane;
+        const int cc = ok[k] ? col[k] : 0;
+        const int b = (int)fdiv((uint32_t)cc, G.div_row);
+        const int a = cc - b * m0;
+        sidx[k] = (b + Q) * pitch + (a + Q);
+        vbase[k] = wrap_once(G.lo[0] + a, P.n[0]) + (long long)P.n[0] * wrap_once(G.lo[1] + b, P.n[1]);
+#pragma unroll
+        for (int t = 0; t <= 2 * Q; ++t) {
+            const int c = t - Q;
+            float2 v = make_float2(0.f, 0.f);
+            if (ok[k] && c >= 0 && c < m2) {
+                const int idx = col[k] + c * plane;
+                const float2 rv = r[idx], pv = p[idx];
+                v = make_float2(rv.x + br * pv.x - bi * pv.y, rv.y + br * pv.y + bi * pv.x);
+                p[idx] = v;
+            }
+            win[k][t] = v;
+        }
+    }
+    for (int c = 0; c < m2; ++c) {
+        float2* buf = sbuf + (c & 1) * bufsz;
+        const int cn = c + Q + 1;
+        const long long voff = nxy * wrap_once(G.lo[2] + c, P.n[2]);
+        float2 nr[K], np[K];
+        float vv[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            nr[k] = make_float2(0.f, 0.f);
+            np[k] = make_float2(0.f, 0.f);
+            vv[k] = 0.f;
+            if (ok[k]) {
+                vv[k] = __ldg(P.V32 + vbase[k] + voff);
+                if (cn < m2) {
+                    nr[k] = r[col[k] + cn * plane];
+                    np[k] = p[col[k] + cn * plane];
+                }
+                buf[sidx[k]] = win[k][Q];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (ok[k]) {
+                const float2 ctr = win[k][Q];
+                const float dg = diag + vv[k] - zr;
+                float yx = dg * ctr.x + zi * ctr.y;
+                float yy = dg * ctr.y - zi * ctr.x;
+                const float2* bp = buf + sidx[k];
+#pragma unroll
+                for (int o = 1; o <= Q; ++o) {
+                    const float wx = cf[0 * kMaxQ + o - 1], wy = cf[1 * kMaxQ + o - 1], wz = cf[2 * kMaxQ + o - 1];
+                    const float2 xp = bp[o], xm = bp[-o];
+                    const float2 yp = bp[o * pitch], ym = bp[-o * pitch];
+                    const float2 zp = win[k][Q + o], zm = win[k][Q - o];
+                    yx += wx * (xp.x + xm.x) + wy * (yp.x + ym.x) + wz * (zp.x + zm.x);
+                    yy += wx * (xp.y + xm.y) + wy * (yp.y + ym.y) + wz * (zp.y + zm.y);
+                }
+                Ap[col[k] + c * plane] = make_float2(yx, yy);
+                acc_re.add(ctr.x * yx - ctr.y * yy);
+                acc_im.add(ctr.x * yy + ctr.y * yx);
+            }
+#pragma unroll
+            for (int t = 0; t < 2 * Q; ++t) win[k][t] = win[k][t + 1];
+            float2 v = make_float2(0.f, 0.f);
+            if (ok[k] && cn < m2) {
+                v = make_float2(nr[k].x + br * np[k].x - bi * np[k].y, nr[k].y + br * np[k].y + bi * np[k].x);
+                p[col[k] + cn * plane] = v;
+            }
+            win[k][2 * Q] = v;
+        }
+    }
+}
+
+// Mixed-precision persistent COCG with the shared-memory z-march stencil
+// (regions without whole-axis rings; stencil half-width Q; K columns per
+// thread, blockDim.x * K >= m0 * m1 for every region of the launch).
+// The nonlocal term enters through the bilinear identity
+//   p^T A p = p^T A_loc p + sum_al E_l dV c_al^2
+// (c from the warp-per-atom dot) and is applied to Ap pointwise in P3.
+template <int Q, int K>
+__global__ void __launch_bounds__(ZmThreads<K>::value) k_cocg_zm(const __grid_constant__ SolveParams P) {
+    using Mode = MixedModeT;
+    using C = float2;
+    __shared__ Shared S;
+    extern __shared__ float2 sbuf[];
+    const uint64_t t_start = global_time_ns();
+    char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
+    for (int t = threadIdx.x; t < 3 * kMaxQ; t += blockDim.x) {
+        (&S.coefD[0][0])[t] = (&P.coef[0][0])[t];
+        (&S.coefF[0][0])[t] = (float)(&P.coef[0][0])[t];
+    }
+    if (P.nonlocal && P.n_atoms <= kMapMax)
+        for (int t = threadIdx.x; t < P.n_atoms; t += blockDim.x) S.map[t] = -1;
+    if (threadIdx.x < 32) S.pnl[threadIdx.x] = make_double2(0.0, 0.0);
+    const float diagF = (float)P.diag;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            S.sys = (int)atomicAdd(P.work_counter, 1u);
+            S.flag = 0;
+        }
+        __syncthreads();
+        const int s = S.sys;
+        if (s >= P.n_sys) break;
+        const SysDesc sd = P.sys[s];
+        const NodeDesc nd = P.nodes[sd.node];
+        Geo G;
+        G.any_ring = 0;
+        for (int d = 0; d < 3; ++d) {
+            G.m[d] = nd.dims[d];
+            G.lo[d] = nd.lo[d];
+            G.ring[d] = 0;
+        }
+        G.plane = G.m[0] * G.m[1];
+        G.n = G.plane * G.m[2];
+        G.src = nd.src;
+        G.div_row = make_fastdiv((uint32_t)G.m[0]);
+        G.div_plane = make_fastdiv((uint32_t)G.plane);
+        const double2 zd = P.z[sd.pole];
+        const float zr = (float)zd.x, zi = (float)zd.y;
+        const long long out_idx = (long long)sd.node * P.P + sd.pole;
+
+        C* r = (C*)slot;
+        C* p = r + P.n_max;
+        C* Ap = p + P.n_max;
+        C* dx = Ap + P.n_max;
+        double2* x = (double2*)(dx + P.n_max);
+        if (P.ckpt) x = P.ckpt + P.ckpt_sys_off[out_idx];
+
+        if (P.nonlocal) collect_local_atoms(P, G, S);
+        {   // zero both plane buffers (their borders stay zero)
+            const int bufsz = (G.m[0] + 2 * Q) * (G.m[1] + 2 * Q);
+            for (int t = threadIdx.x; t < 2 * bufsz; t += blockDim.x) sbuf[t] = make_float2(0.f, 0.f);
+        }
+        for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
+            r[i] = make_float2(i == G.src ? 1.f : 0.f, 0.f);
+            p[i] = make_float2(0.f, 0.f);
+            x[i] = make_double2(0.0, 0.0);
+            dx[i] = make_float2(0.f, 0.f);
+        }
+        if (threadIdx.x == 0) {
+            S.beta[0] = 0.0;
+            S.beta[1] = 0.0;
+            S.action = 0;
+            S.rho[0] = 1.0;
+            S.rho[1] = 0.0;
+            S.rn = 1.0;
+            S.rn_last = 1.0;
+            S.it = 0;
+            S.last_rel = 0;
+            S.n_rel = 0;
+            S.st = 2;
+        }
+        __syncthreads();
+
+        for (;;) {
+            if (P.timeout_ns && threadIdx.x == 0 && (global_time_ns() - t_start) > P.timeout_ns)
+                S.action = kStopTimeout;
+            if (threadIdx.x == 0 && S.it >= P.maxit) S.action = kStop;
+            __syncthreads();
+            if (S.action == kStop || S.action == kStopTimeout) break;
+            KSum<float> acc_re, acc_im;
+            zm_stencil_pass<Q, K>(P, G, S, sbuf, r, p, Ap, (float)S.beta[0], (float)S.beta[1], zr, zi,
+                                  diagF, acc_re, acc_im);
+            __syncthreads();
+            if (P.nonlocal) nonlocal_coeffs<float, float2>(P, G, S, p);
+            {
+                double pap[2] = {acc_re.get(), acc_im.get()};
+                if (P.nonlocal && (threadIdx.x & 31) == 0) {
+                    pap[0] += S.pnl[threadIdx.x >> 5].x;
+                    pap[1] += S.pnl[threadIdx.x >> 5].y;
+                }
+                block_reduce<2>(S, pap);
+                if (threadIdx.x == 0) {
+                    ++S.it;
+                    const double den = pap[0] * pap[0] + pap[1] * pap[1];
+                    if (!(den > 0.0)) {
+                        S.st = 3;
+                        S.action = kStop;
+                    } else {
+                        S.alpha[0] = (S.rho[0] * pap[0] + S.rho[1] * pap[1]) / den;
+                        S.alpha[1] = (S.rho[1] * pap[0] - S.rho[0] * pap[1]) / den;
+                    }
+                }
+                __syncthreads();
+                if (S.action == kStop) break;
+            }
+            double red3[3];
+            {   // P3: dx += alpha p ; r -= alpha (Ap_loc + Ap_nl) ; r^T r ; |r|^2
+                const float ar = (float)S.alpha[0], ai = (float)S.alpha[1];
+                KSum<float> s_re, s_im, s_n;
+                const float4* p4 = reinterpret_cast<const float4*>(p);
+                const float4* q4 = reinterpret_cast<const float4*>(Ap);
+                float4* d4 = reinterpret_cast<float4*>(dx);
+                float4* r4 = reinterpret_cast<float4*>(r);
+                const int npair = G.n >> 1;
+                for (int k = threadIdx.x; k < npair; k += blockDim.x) {
+                    const float4 pv = p4[k];
+                    float4 qv = q4[k];
+                    if (P.nonlocal) {
+                        const float2 n0 = nl_apply(P, G, S, 2 * k), n1 = nl_apply(P, G, S, 2 * k + 1);
+                        qv.x += n0.x; qv.y += n0.y; qv.z += n1.x; qv.w += n1.y;
+                    }
+                    float4 d = d4[k], rv = r4[k];
+                    d.x += ar * pv.x - ai * pv.y;
+                    d.y += ar * pv.y + ai * pv.x;
+                    d.z += ar * pv.z - ai * pv.w;
+                    d.w += ar * pv.w + ai * pv.z;
+                    rv.x -= ar * qv.x - ai * qv.y;
+                    rv.y -= ar * qv.y + ai * qv.x;
+                    rv.z -= ar * qv.z - ai * qv.w;
+                    rv.w -= ar * qv.w + ai * qv.z;
+                    d4[k] = d;
+                    r4[k] = rv;
+                    s_re.add(rv.x * rv.x - rv.y * rv.y + (rv.z * rv.z - rv.w * rv.w));
+                    s_im.add(2.f * (rv.x * rv.y + rv.z * rv.w));
+                    s_n.add(rv.x * rv.x + rv.y * rv.y + (rv.z * rv.z + rv.w * rv.w));
+                }
+                if ((G.n & 1) && threadIdx.x == 0) {
+                    const int i = G.n - 1;
+                    const C pi = p[i];
+                    C api = Ap[i];
+                    if (P.nonlocal) {
+                        const float2 n0 = nl_apply(P, G, S, i);
+                        api.x += n0.x;
+                        api.y += n0.y;
+                    }
+                    C d = dx[i], ri = r[i];
+                    d.x += ar * pi.x - ai * pi.y;
+                    d.y += ar * pi.y + ai * pi.x;
+                    ri.x -= ar * api.x - ai * api.y;
+                    ri.y -= ar * api.y + ai * api.x;
+                    dx[i] = d;
+                    r[i] = ri;
+                    s_re.add(ri.x * ri.x - ri.y * ri.y);
+                    s_im.add(2.f * ri.x * ri.y);
+                    s_n.add(ri.x * ri.x + ri.y * ri.y);
+                }
+                red3[0] = s_re.get();
+                red3[1] = s_im.get();
+                red3[2] = s_n.get();
+                block_reduce<3>(S, red3);
+            }
+            if (threadIdx.x == 0) {
+                const double rn = sqrt(red3[2]);
+                const bool want = (rn <= P.tol) || (S.it - S.last_rel >= P.reliable_every) ||
+                                  (rn < P.reliable_delta * S.rn_last);
+                S.action = want ? kRefresh : 0;
+            }
+            __syncthreads();
+            if (S.action == kRefresh) {
+                refresh_residual<Mode, Q>(P, G, S, r, dx, x, zd, red3);
+                if (threadIdx.x == 0) {
+                    S.rn_last = sqrt(red3[2]);
+                    S.last_rel = S.it;
+                    ++S.n_rel;
+                }
+            }
+            if (threadIdx.x == 0) {
+                const double rn = sqrt(red3[2]);
+                S.rn = rn;
+                S.action = 0;
+                const double rr_abs = sqrt(red3[0] * red3[0] + red3[1] * red3[1]);
+                if (rn <= P.tol) {
+                    S.st = 0;
+                    S.action = kStop;
+                } else if (!(rr_abs > 1e-300) || rr_abs < 1e-14 * rn * rn) {
+                    S.st = 3;
+                    S.action = kStop;
+                } else {
+                    const double rd = S.rho[0] * S.rho[0] + S.rho[1] * S.rho[1];
+                    S.beta[0] = (red3[0] * S.rho[0] + red3[1] * S.rho[1]) / rd;
+                    S.beta[1] = (red3[1] * S.rho[0] - red3[0] * S.rho[1]) / rd;
+                    S.rho[0] = red3[0];
+                    S.rho[1] = red3[1];
+                }
+            }
+            __syncthreads();
+            if (S.action == kStop) break;
+        }
+        const bool timed_out = (S.action == kStopTimeout);
+        __syncthreads();
+        const int status = S.st;
+        if (status != 0) {
+            for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
+                const C d = dx[i];
+                double2 xv = x[i];
+                xv.x += (double)d.x;
+                xv.y += (double)d.y;
+                x[i] = xv;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            P.x_src[out_idx] = x[G.src];
+            P.status[out_idx] = timed_out ? 4 : (S.flag ? 1 : status);
+            P.iters[out_idx] = S.it;
+            P.resid[out_idx] = S.rn;
+            P.n_rel[out_idx] = S.n_rel;
+        }
+        if (P.nonlocal) release_local_atoms(P, S);
+        __syncthreads();
+    }
+}
+
 struct FP64Mode {
     using real = double;
     using cplx = double2;
     static constexpr bool kMixed = false;
 };
-struct MixedMode {
-    using real = float;
-    using cplx = float2;
-    static constexpr bool kMixed = true;
-};
+using MixedMode = MixedModeT;
 
 template <class Mode>
 cudaError_t launch_q(const SolveParams& P, int grid, int block, cudaStream_t stream) {
@@ -807,7 +1188,81 @@ cudaError_t launch_q(const SolveParams& P, int grid, int block, cudaStream_t str
     return cudaGetLastError();
 }
 
+template <int Q, int K>
+cudaError_t launch_zm_k(const SolveParams& P, int grid, int block, size_t smem, cudaStream_t stream) {
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_cocg_zm<Q, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        configured = true;
+    }
+    k_cocg_zm<Q, K><<<grid, block, smem, stream>>>(P);
+    return cudaGetLastError();
+}
+
+template <int Q>
+cudaError_t launch_zm_q(const SolveParams& P, int K, int grid, int block, size_t smem, cudaStream_t stream) {
+    switch (K) {
+        case 1: return launch_zm_k<Q, 1>(P, grid, block, smem, stream);
+        case 2: return launch_zm_k<Q, 2>(P, grid, block, smem, stream);
+        case 3: return launch_zm_k<Q, 3>(P, grid, block, smem, stream);
+        case 4: return launch_zm_k<Q, 4>(P, grid, block, smem, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
+
+int zm_max_threads(int K) {
+    switch (K) {
+        case 1: return ZmThreads<1>::value;
+        case 2: return ZmThreads<2>::value;
+        case 3: return ZmThreads<3>::value;
+        case 4: return ZmThreads<4>::value;
+        default: return 0;
+    }
+}
+
+bool zm_supported(int precision, int q) { return precision == MD_PREC_MIXED && (q == 2 || q == 4); }
+
+template <int Q, int K>
+int zm_occ_k(int block, size_t smem) {
+    cudaFuncSetAttribute(k_cocg_zm<Q, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cocg_zm<Q, K>, block, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+int zm_occupancy(int q, int K, int block, size_t smem) {
+    if (q == 2) {
+        switch (K) {
+            case 1: return zm_occ_k<2, 1>(block, smem);
+            case 2: return zm_occ_k<2, 2>(block, smem);
+            case 3: return zm_occ_k<2, 3>(block, smem);
+            case 4: return zm_occ_k<2, 4>(block, smem);
+        }
+    } else if (q == 4) {
+        switch (K) {
+            case 1: return zm_occ_k<4, 1>(block, smem);
+            case 2: return zm_occ_k<4, 2>(block, smem);
+            case 3: return zm_occ_k<4, 3>(block, smem);
+            case 4: return zm_occ_k<4, 4>(block, smem);
+        }
+    }
+    return 0;
+}
+
+size_t zm_smem_bytes(int q, int max_m0, int max_m1) {
+    return 2 * sizeof(float2) * (size_t)(max_m0 + 2 * q) * (size_t)(max_m1 + 2 * q);
+}
+
+cudaError_t launch_cocg_zm(const SolveParams& P, int K, int grid, int block, size_t smem, cudaStream_t stream) {
+    if (P.q == 2) return launch_zm_q<2>(P, K, grid, block, smem, stream);
+    if (P.q == 4) return launch_zm_q<4>(P, K, grid, block, smem, stream);
+    return cudaErrorInvalidValue;
+}
 
 size_t slot_bytes_for(int precision, long long n_max) {
     const size_t nm = (size_t)((n_max + 63) / 64 * 64);

@@ -77,6 +77,13 @@ struct SolveParams {
 };
 
 size_t slot_bytes_for(int precision, long long n_max);
+// Shared-memory z-march variant (mixed precision, stencil half-width 2 or 4,
+// regions without whole-axis rings); K columns per thread.
+bool zm_supported(int precision, int q);
+int zm_max_threads(int K);
+size_t zm_smem_bytes(int q, int max_m0, int max_m1);
+int zm_occupancy(int q, int K, int block, size_t smem);   // resident CTAs per SM
+cudaError_t launch_cocg_zm(const SolveParams& P, int K, int grid, int block, size_t smem, cudaStream_t stream);
 cudaError_t launch_cocg(const SolveParams& P, int precision, int grid, int block, cudaStream_t stream);
 cudaError_t launch_accumulate(int n_nodes, int Pn, const double2* x_src, const double2* z,
                               const double2* w, double dV, double* rho, double* e, cudaStream_t stream);
