@@ -109,9 +109,11 @@ typedef struct {
     int32_t maxit;         /* iteration cap per system, > 0 */
     int32_t precision;     /* md_precision */
     int32_t reliable_every;/* mixed: max iterations between FP64 residual
-                              recomputations (0 = 1000) */
+                              recomputations (0 = 200) */
     double reliable_delta; /* mixed: also recompute when ||r|| fell by this
-                              factor since the last one (0 = 1e-3) */
+                              factor since the last one (0 = 1e-2); a refresh
+                              that finds the residual larger than at the
+                              previous one restarts the Krylov recurrence */
     double timeout_s;      /* device wall-clock budget for the call, 0 = none */
     int32_t block;         /* threads per CTA; 0 = library choice */
     int32_t ctas_per_sm;   /* resident CTAs per SM; 0 = library choice */

@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -174,8 +176,8 @@ md_solver_opts normalise_opts(const md_solver_opts* o) {
     md_solver_opts r;
     std::memset(&r, 0, sizeof(r));
     if (o) r = *o;
-    if (r.reliable_every <= 0) r.reliable_every = 1000;
-    if (!(r.reliable_delta > 0.0)) r.reliable_delta = 1e-3;
+    if (r.reliable_every <= 0) r.reliable_every = 200;
+    if (!(r.reliable_delta > 0.0)) r.reliable_delta = 1e-2;
     return r;
 }
 
@@ -356,6 +358,9 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
         long long pit = 0;
         for (const auto& sd : sample) pit += (long long)h_it[(long long)sd.node * pl->Pn + sd.pole] * pl->points[sd.node];
         const double rate = ms > 0 ? (double)pit / ms : 0.0;
+        if (std::getenv("MD_AUTOTUNE_LOG"))
+            std::fprintf(stderr, "md autotune: variant %d block %d ctas/SM %d: %.3f ms, %.3g point-iterations/s\n",
+                         c.variant, c.block, c.per_sm, ms, rate * 1e3);
         if (rate > best) {
             best = rate;
             bs = c;

@@ -133,6 +133,7 @@ struct Shared {
     double rho[2];        // r^T r
     double rn, rn_last;   // ||r||, ||r|| at the last residual refresh
     int it, last_rel, n_rel, st;
+    int restart;
     int action;
     int status;
     int sys;
@@ -595,6 +596,7 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
             S.it = 0;
             S.last_rel = 0;
             S.n_rel = 0;
+            S.restart = 0;
             S.st = 2;   // not converged
         }
         __syncthreads();
@@ -730,7 +732,10 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                 if (S.action == kRefresh) {
                     refresh_residual<Mode, Q>(P, G, S, r, dx, x, zd, red3);
                     if (threadIdx.x == 0) {
-                        S.rn_last = sqrt(red3[2]);
+                        const double rt = sqrt(red3[2]);
+                        // no progress since the previous refresh: restart (p = r next)
+                        S.restart = (S.n_rel > 0 && rt >= S.rn_last) ? 1 : 0;
+                        S.rn_last = rt;
                         S.last_rel = S.it;
                         ++S.n_rel;
                     }
@@ -749,11 +754,12 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                     S.action = kStop;
                 } else {
                     const double rd = S.rho[0] * S.rho[0] + S.rho[1] * S.rho[1];
-                    S.beta[0] = (red3[0] * S.rho[0] + red3[1] * S.rho[1]) / rd;
-                    S.beta[1] = (red3[1] * S.rho[0] - red3[0] * S.rho[1]) / rd;
+                    S.beta[0] = S.restart ? 0.0 : (red3[0] * S.rho[0] + red3[1] * S.rho[1]) / rd;
+                    S.beta[1] = S.restart ? 0.0 : (red3[1] * S.rho[0] - red3[0] * S.rho[1]) / rd;
                     S.rho[0] = red3[0];
                     S.rho[1] = red3[1];
                 }
+                S.restart = 0;
             }
             __syncthreads();
             if (S.action == kStop) break;
@@ -1011,6 +1017,7 @@ __global__ void __launch_bounds__(ZmThreads<K>::value) k_cocg_zm(const __grid_co
             S.it = 0;
             S.last_rel = 0;
             S.n_rel = 0;
+            S.restart = 0;
             S.st = 2;
         }
         __syncthreads();
@@ -1113,7 +1120,9 @@ __global__ void __launch_bounds__(ZmThreads<K>::value) k_cocg_zm(const __grid_co
             if (S.action == kRefresh) {
                 refresh_residual<Mode, Q>(P, G, S, r, dx, x, zd, red3);
                 if (threadIdx.x == 0) {
-                    S.rn_last = sqrt(red3[2]);
+                    const double rt = sqrt(red3[2]);
+                    S.restart = (S.n_rel > 0 && rt >= S.rn_last) ? 1 : 0;
+                    S.rn_last = rt;
                     S.last_rel = S.it;
                     ++S.n_rel;
                 }
@@ -1131,11 +1140,12 @@ __global__ void __launch_bounds__(ZmThreads<K>::value) k_cocg_zm(const __grid_co
                     S.action = kStop;
                 } else {
                     const double rd = S.rho[0] * S.rho[0] + S.rho[1] * S.rho[1];
-                    S.beta[0] = (red3[0] * S.rho[0] + red3[1] * S.rho[1]) / rd;
-                    S.beta[1] = (red3[1] * S.rho[0] - red3[0] * S.rho[1]) / rd;
+                    S.beta[0] = S.restart ? 0.0 : (red3[0] * S.rho[0] + red3[1] * S.rho[1]) / rd;
+                    S.beta[1] = S.restart ? 0.0 : (red3[1] * S.rho[0] - red3[0] * S.rho[1]) / rd;
                     S.rho[0] = red3[0];
                     S.rho[1] = red3[1];
                 }
+                S.restart = 0;
             }
             __syncthreads();
             if (S.action == kStop) break;
