@@ -203,7 +203,7 @@ def main():
     torch.cuda.set_device(local)
     from synthetic import make_workload
     from paper_1907_02604_gb300 import Hamiltonian, Plan, SolverOptions, density, make_poles
-    from paper_1907_02604_gb300 import _lib
+    from paper_1907_02604_gb300.sharding import batch_slice
 
     w = make_workload(args.workload)
     prec = args.precision or w.precision
@@ -215,8 +215,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     def batch(i):
-        b = (i * world + rank) % n_batches
-        sl = slice(b * bs, (b + 1) * bs)
+        sl = batch_slice(n_nodes, bs, world, rank, i)
         return w.nodes[sl], w.halfwidth[sl]
 
     # ---- device-resident inputs: Hamiltonian built and batches planned -----
