@@ -65,6 +65,8 @@ struct KSum<float> {
         s = t;
     }
     __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+    __device__ __forceinline__ float hi() const { return s; }
+    __device__ __forceinline__ float lo() const { return -c; }
 };
 struct MixedModeT {
     using real = float;
@@ -153,6 +155,52 @@ template <>
 __device__ __forceinline__ const double* coef_of<double>(const Shared& S) { return &S.coefD[0][0]; }
 template <>
 __device__ __forceinline__ const float* coef_of<float>(const Shared& S) { return &S.coefF[0][0]; }
+
+// Error-free float-float addition (Knuth's TwoSum on the high parts, the
+// low parts added in): keeps ~48 significant bits on the FP32 pipe.
+__device__ __forceinline__ void ff_add(float& ah, float& al, float bh, float bl) {
+    const float s = ah + bh;
+    const float v = s - ah;
+    const float e = (ah - (s - v)) + (bh - v) + (al + bl);
+    ah = s + e;
+    al = e - (ah - s);
+}
+
+// Block-wide sum of K per-thread float-float partials (hi, lo): the warp
+// stage stays in float-float, the 32 warp totals are summed in double by
+// warp 0.  Only thread 0 holds the totals afterwards (in v).
+template <int K>
+__device__ __forceinline__ void block_reduce_ff(Shared& S, const float (&hi)[K], const float (&lo)[K],
+                                                double (&v)[K]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float h[K], l[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        h[k] = hi[k];
+        l[k] = lo[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float bh = __shfl_xor_sync(0xffffffffu, h[k], o);
+            const float bl = __shfl_xor_sync(0xffffffffu, l[k], o);
+            ff_add(h[k], l[k], bh, bl);
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) S.red[warp][k] = (double)h[k] + (double)l[k];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = lane < nw ? S.red[lane][k] : 0.0;
+            v[k] = warp_sum(t);
+        }
+    }
+}
 
 // Block-wide sum of K doubles; only thread 0 holds the totals afterwards.
 template <int K>
@@ -351,8 +399,10 @@ __device__ void nonlocal_coeffs(const SolveParams& P, const Geo& G, Shared& S, c
             acc[6] += ez * Ar;  acc[7] += ez * Ai;
         }
         double s[8];
+        // warp sums in R (float in the mixed iteration: the FP64 pipe is
+        // scarce), then one conversion of the warp total
 #pragma unroll
-        for (int t = 0; t < 8; ++t) s[t] = warp_sum((double)acc[t]);
+        for (int t = 0; t < 8; ++t) s[t] = (double)warp_sum(acc[t]);
         if (lane < 4) {
             const double Cl = (double)__ldg(P.proj_C + 4LL * a + lane);
             const double E = (lane == 0 ? P.e_s : P.e_p) * P.dV * Cl;
@@ -642,8 +692,15 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                     acc_re.add(pi.x * y.x - pi.y * y.y);
                     acc_im.add(pi.x * y.y + pi.y * y.x);
                 }
-                double pap[2] = {acc_re.get(), acc_im.get()};
-                block_reduce<2>(S, pap);
+                double pap[2];
+                if constexpr (Mode::kMixed) {
+                    const float hi[2] = {acc_re.hi(), acc_im.hi()}, lo[2] = {acc_re.lo(), acc_im.lo()};
+                    block_reduce_ff<2>(S, hi, lo, pap);
+                } else {
+                    pap[0] = acc_re.get();
+                    pap[1] = acc_im.get();
+                    block_reduce<2>(S, pap);
+                }
                 if (threadIdx.x == 0) {
                     ++S.it;
                     const double den = pap[0] * pap[0] + pap[1] * pap[1];
@@ -716,10 +773,16 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                         s_n.add(ri.x * ri.x + ri.y * ri.y);
                     }
                 }
-                red3[0] = s_re.get();
-                red3[1] = s_im.get();
-                red3[2] = s_n.get();
-                block_reduce<3>(S, red3);
+                if constexpr (Mode::kMixed) {
+                    const float hi[3] = {s_re.hi(), s_im.hi(), s_n.hi()};
+                    const float lo[3] = {s_re.lo(), s_im.lo(), s_n.lo()};
+                    block_reduce_ff<3>(S, hi, lo, red3);
+                } else {
+                    red3[0] = s_re.get();
+                    red3[1] = s_im.get();
+                    red3[2] = s_n.get();
+                    block_reduce<3>(S, red3);
+                }
             }
             if (Mode::kMixed) {
                 if (threadIdx.x == 0) {
@@ -1034,12 +1097,15 @@ __global__ void __launch_bounds__(ZmThreads<K>::value) k_cocg_zm(const __grid_co
             __syncthreads();
             if (P.nonlocal) nonlocal_coeffs<float, float2>(P, G, S, p);
             {
-                double pap[2] = {acc_re.get(), acc_im.get()};
+                float hi[2] = {acc_re.hi(), acc_im.hi()}, lo[2] = {acc_re.lo(), acc_im.lo()};
                 if (P.nonlocal && (threadIdx.x & 31) == 0) {
-                    pap[0] += S.pnl[threadIdx.x >> 5].x;
-                    pap[1] += S.pnl[threadIdx.x >> 5].y;
+                    const double2 q = S.pnl[threadIdx.x >> 5];
+                    const float qr = (float)q.x, qi = (float)q.y;
+                    ff_add(hi[0], lo[0], qr, (float)(q.x - (double)qr));
+                    ff_add(hi[1], lo[1], qi, (float)(q.y - (double)qi));
                 }
-                block_reduce<2>(S, pap);
+                double pap[2];
+                block_reduce_ff<2>(S, hi, lo, pap);
                 if (threadIdx.x == 0) {
                     ++S.it;
                     const double den = pap[0] * pap[0] + pap[1] * pap[1];
@@ -1105,10 +1171,9 @@ __global__ void __launch_bounds__(ZmThreads<K>::value) k_cocg_zm(const __grid_co
                     s_im.add(2.f * ri.x * ri.y);
                     s_n.add(ri.x * ri.x + ri.y * ri.y);
                 }
-                red3[0] = s_re.get();
-                red3[1] = s_im.get();
-                red3[2] = s_n.get();
-                block_reduce<3>(S, red3);
+                const float hi3[3] = {s_re.hi(), s_im.hi(), s_n.hi()};
+                const float lo3[3] = {s_re.lo(), s_im.lo(), s_n.lo()};
+                block_reduce_ff<3>(S, hi3, lo3, red3);
             }
             if (threadIdx.x == 0) {
                 const double rn = sqrt(red3[2]);
