@@ -255,6 +255,43 @@ md_status md_density_adjoint(const md_hamiltonian* ham, const md_poles* poles,
                              md_workspace* ckpt, double* dL_dV_out,
                              double* forces_out, md_stats* stats, void* stream);
 
+/* ---- Density without device allocation ---------------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they solve -- a process whose GPU
+ * memory is owned by another allocator with a fixed budget (a framework's
+ * caching allocator, a serving engine that reserves its memory at start-up)
+ * or code running where an allocation would synchronise or be refused.  It
+ * computes what md_density computes (rho_out and, if non-NULL, e_out:
+ * device, n_nodes doubles; stats as in md_density) but keeps every
+ * temporary (Krylov vectors, work list, descriptors, per-system results)
+ * in one static device array of MD_NOALLOC_SCRATCH_BYTES of Krylov space
+ * plus room for MD_NOALLOC_MAX_SYSTEMS systems, which every GPU that loads
+ * the library holds until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine, and nothing on the host heap on
+ * success (error messages excepted).  The Hamiltonian must be built
+ * beforehand (md_build_hamiltonian allocates).
+ *   - Limits: n_nodes <= MD_NOALLOC_MAX_NODES, P <= MD_NOALLOC_MAX_POLES,
+ *     n_nodes * P <= MD_NOALLOC_MAX_SYSTEMS, and one region's Krylov slot
+ *     (48 B per point mixed, 64 B per point FP64) within
+ *     MD_NOALLOC_SCRATCH_BYTES; beyond them it returns MD_ERR_INVALID with
+ *     nothing launched.  Concurrency is one CTA per SM, capped by the number
+ *     of slots that fit, so large regions run on fewer SMs.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call shares the array, which keeps the last call's contents;
+ *     the call zeroes what must start at zero.  Calls that overlap on the
+ *     GPU race on the array and corrupt each other's results.  Calls made
+ *     through this entry point in one process take a host lock and each
+ *     synchronises its stream before returning, so they do not overlap. */
+#define MD_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define MD_NOALLOC_MAX_SYSTEMS 16384
+#define MD_NOALLOC_MAX_NODES 4096
+#define MD_NOALLOC_MAX_POLES 64
+md_status md_density_noalloc(const md_hamiltonian* ham, const md_poles* poles,
+                             const md_nodes* nodes, const md_solver_opts* opts,
+                             double* rho_out, double* e_out, md_stats* stats, void* stream);
+
 /* Central weights w_0..w_q (q = order/2) of d^2/dx^2 on a unit grid with
  * accuracy order `order` (even, 2..16), by Fornberg's recursion (Math.
  * Comp. 51 (1988)); the library's Laplacian is -1/2 sum_d w / h_d^2 (the

@@ -96,6 +96,9 @@ SIGNATURES = [
     ("md_plan_launch_shape", ctypes.c_int, [_VP, c_int32_p, c_int32_p]),
     ("md_plan_system_info", ctypes.c_int, [_VP, _VP, c_int32_p, c_int32_p, c_double_p]),
     ("md_plan_destroy", ctypes.c_int, [_VP]),
+    ("md_density_noalloc", ctypes.c_int, [_VP, ctypes.POINTER(md_poles), ctypes.POINTER(md_nodes),
+                                          ctypes.POINTER(md_solver_opts), _VP, _VP,
+                                          ctypes.POINTER(md_stats), _VP]),
     ("md_fd_weights", ctypes.c_int, [ctypes.c_int32, c_double_p]),
     ("md_last_error", ctypes.c_char_p, []),
     ("md_version", ctypes.c_char_p, []),

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -633,6 +634,257 @@ md_status density_impl(const md_hamiltonian* ham, const md_poles* poles, const m
 
 }  // namespace
 }  // namespace md
+
+// ---------------------------------------------------------------------------
+// Density without device allocation (md_density_noalloc).
+//
+// For callers that cannot allocate device memory while they solve: a
+// process whose GPU memory is owned by another allocator with a fixed
+// budget (a framework's caching allocator, a serving engine that reserves
+// its memory at start-up), or code running where an allocation would
+// synchronise or be refused.  All device storage of the call (Krylov slots,
+// work list, region descriptors, poles, per-system results, the work
+// counter) lives in the file-scope array below, so the call itself allocates
+// nothing on the device and nothing on the host heap on its success path.
+// The Hamiltonian must have been built beforehand.
+// ---------------------------------------------------------------------------
+namespace md {
+namespace {
+
+constexpr size_t kNaScratchBytes = (size_t)MD_NOALLOC_SCRATCH_BYTES;
+constexpr long long kNaMaxSystems = MD_NOALLOC_MAX_SYSTEMS;
+constexpr long long kNaMaxNodes = MD_NOALLOC_MAX_NODES;
+constexpr int kNaMaxPoles = MD_NOALLOC_MAX_POLES;
+
+// layout of the static array: [descriptors and results | Krylov slots]
+constexpr size_t kNaOffSys = 0;
+constexpr size_t kNaOffNodes = kNaOffSys + sizeof(SysDesc) * kNaMaxSystems;
+constexpr size_t kNaOffZ = kNaOffNodes + sizeof(NodeDesc) * kNaMaxNodes;
+constexpr size_t kNaOffW = kNaOffZ + sizeof(double2) * kNaMaxPoles;
+constexpr size_t kNaOffXsrc = kNaOffW + sizeof(double2) * kNaMaxPoles;
+constexpr size_t kNaOffStatus = kNaOffXsrc + sizeof(double2) * kNaMaxSystems;
+constexpr size_t kNaOffIters = kNaOffStatus + sizeof(int) * kNaMaxSystems;
+constexpr size_t kNaOffNrel = kNaOffIters + sizeof(int) * kNaMaxSystems;
+constexpr size_t kNaOffResid = kNaOffNrel + sizeof(int) * kNaMaxSystems;
+constexpr size_t kNaOffCounter = kNaOffResid + sizeof(double) * kNaMaxSystems;
+constexpr size_t kNaOffSlots = (kNaOffCounter + sizeof(unsigned int) + 255) / 256 * 256;
+constexpr size_t kNaTotalBytes = kNaOffSlots + kNaScratchBytes;
+
+// Held by every GPU that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_area[kNaTotalBytes];
+
+std::mutex g_na_mutex;                       // host buffers below are shared
+char* g_na_dev_ptr[64] = {nullptr};          // device address of the array, per device
+SysDesc g_na_sys[kNaMaxSystems];
+NodeDesc g_na_nodes[kNaMaxNodes];
+long long g_na_points[kNaMaxNodes];
+int g_na_status[kNaMaxSystems];
+int g_na_iters[kNaMaxSystems];
+int g_na_nrel[kNaMaxSystems];
+double g_na_resid[kNaMaxSystems];
+
+}  // namespace
+}  // namespace md
+
+extern "C" md_status md_density_noalloc(const md_hamiltonian* ham, const md_poles* poles,
+                                        const md_nodes* nodes, const md_solver_opts* opts,
+                                        double* rho_out, double* e_out, md_stats* stats,
+                                        void* stream_) {
+    using namespace md;
+    clear_error();
+    std::lock_guard<std::mutex> guard(g_na_mutex);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    md_status st = check_device();
+    if (st != MD_OK) return st;
+    if (!ham) return set_error(MD_ERR_INVALID, "ham is NULL");
+    if ((st = check_poles(poles)) != MD_OK) return st;
+    if ((st = check_opts(opts)) != MD_OK) return st;
+    if (!nodes || nodes->n_nodes < 0 || (nodes->n_nodes > 0 && (!nodes->node || !nodes->halfwidth)))
+        return set_error(MD_ERR_INVALID, "nodes: null arrays or negative count");
+    const Ham& H = ham->h;
+    const long long nn = nodes->n_nodes;
+    const int Pn = poles->n_poles;
+    if (nn == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return MD_OK;
+    }
+    if (!rho_out) return set_error(MD_ERR_INVALID, "rho_out is NULL");
+    if (nn > kNaMaxNodes || Pn > kNaMaxPoles || nn * Pn > kNaMaxSystems)
+        return set_error(MD_ERR_INVALID,
+                         "md_density_noalloc: more than MD_NOALLOC_MAX_NODES nodes, "
+                         "MD_NOALLOC_MAX_POLES poles or MD_NOALLOC_MAX_SYSTEMS systems");
+    // region descriptors, as md_density builds them, into the static host buffers
+    long long n_max = 0;
+    for (long long j = 0; j < nn; ++j) {
+        const long long g = nodes->node[j];
+        const int s = nodes->halfwidth[j];
+        if (g < 0 || g >= H.N) return set_error(MD_ERR_INVALID, "node index out of range");
+        if (s < 0) return set_error(MD_ERR_INVALID, "negative region half-width");
+        const int c[3] = {(int)(g % H.n[0]), (int)((g / H.n[0]) % H.n[1]),
+                          (int)(g / ((long long)H.n[0] * H.n[1]))};
+        NodeDesc& d = g_na_nodes[j];
+        d.ring = 0;
+        int srcc[3];
+        long long pts = 1;
+        for (int ax = 0; ax < 3; ++ax) {
+            const long long m = 2LL * s + 1;
+            if (H.periodic[ax] && m >= H.n[ax]) {
+                d.dims[ax] = H.n[ax];
+                d.lo[ax] = 0;
+                d.ring |= 1 << ax;
+                srcc[ax] = c[ax];
+            } else {
+                if (!H.periodic[ax] && (c[ax] - s < 0 || c[ax] + s >= H.n[ax]))
+                    return set_error(MD_ERR_INVALID, "region leaves a non-periodic grid axis");
+                d.dims[ax] = (int)m;
+                d.lo[ax] = c[ax] - s;
+                srcc[ax] = s;
+            }
+            pts *= d.dims[ax];
+        }
+        if (pts > (1LL << 30)) return set_error(MD_ERR_INVALID, "region too large");
+        d.src = srcc[0] + d.dims[0] * (srcc[1] + d.dims[1] * srcc[2]);
+        g_na_points[j] = pts;
+        n_max = std::max(n_max, pts);
+    }
+    const md_solver_opts o = normalise_opts(opts);
+    const size_t slot = slot_bytes_for(o.precision, n_max);
+    if (slot > kNaScratchBytes)
+        return set_error(MD_ERR_INVALID,
+                         "md_density_noalloc: one region's Krylov vectors exceed MD_NOALLOC_SCRATCH_BYTES");
+    int dev = 0, n_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return set_error(MD_ERR_CUDA, "device ordinal beyond 63");
+    // set-up, once per device with that device current: the device address
+    // of the static array (its host-side name is only a stand-in)
+    if (!g_na_dev_ptr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_area);
+        if (e != cudaSuccess || !ptr)
+            return set_error(MD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_na_dev_ptr[dev] = (char*)ptr;
+    }
+    char* base = g_na_dev_ptr[dev];
+    const long long n_sys = nn * Pn;
+    for (long long j = 0; j < nn; ++j)
+        for (int p = 0; p < Pn; ++p) g_na_sys[j * Pn + p] = SysDesc{(int)j, p};
+    std::sort(g_na_sys, g_na_sys + n_sys, [&](const SysDesc& a, const SysDesc& b) {
+        const double ca = (double)g_na_points[a.node] / std::sqrt(poles->z[2 * a.pole + 1]);
+        const double cb = (double)g_na_points[b.node] / std::sqrt(poles->z[2 * b.pole + 1]);
+        if (ca != cb) return ca > cb;
+        return a.node != b.node ? a.node < b.node : a.pole < b.pole;
+    });
+    SysDesc* d_sys = (SysDesc*)(base + kNaOffSys);
+    NodeDesc* d_nodes = (NodeDesc*)(base + kNaOffNodes);
+    double2* d_z = (double2*)(base + kNaOffZ);
+    double2* d_w = (double2*)(base + kNaOffW);
+    double2* d_xsrc = (double2*)(base + kNaOffXsrc);
+    int* d_status = (int*)(base + kNaOffStatus);
+    int* d_iters = (int*)(base + kNaOffIters);
+    int* d_nrel = (int*)(base + kNaOffNrel);
+    double* d_resid = (double*)(base + kNaOffResid);
+    unsigned int* d_counter = (unsigned int*)(base + kNaOffCounter);
+    char* slots = base + kNaOffSlots;
+    e = cudaMemcpyAsync(d_sys, g_na_sys, n_sys * sizeof(SysDesc), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_nodes, g_na_nodes, nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_z, poles->z, Pn * sizeof(double2), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, poles->w, Pn * sizeof(double2), cudaMemcpyHostToDevice, stream);
+    // the array keeps the previous call's contents: the work counter must start at zero
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
+    if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+
+    SolveParams P;
+    std::memset(&P, 0, sizeof(P));
+    for (int d = 0; d < 3; ++d) {
+        P.n[d] = H.n[d];
+        P.periodic[d] = H.periodic[d];
+        for (int q = 0; q < kMaxQ; ++q) P.coef[d][q] = H.coef[d][q];
+    }
+    P.N = H.N;
+    P.q = H.q;
+    P.diag = H.diag;
+    P.dV = H.dV;
+    P.V = H.V;
+    P.V32 = H.V32;
+    P.nonlocal = H.nonlocal && H.n_atoms > 0;
+    P.n_atoms = H.n_atoms;
+    P.proj_i0 = H.proj_i0;
+    P.proj_len = H.proj_len;
+    P.proj_d = H.proj_d;
+    P.proj_g = H.proj_g;
+    P.proj_d32 = H.proj_d32;
+    P.proj_g32 = H.proj_g32;
+    P.proj_C = H.proj_C;
+    P.proj_C32 = H.proj_C32;
+    P.proj_rows = H.proj_rows;
+    P.pl_ptr = H.pl_ptr;
+    P.pl_atom = H.pl_atom;
+    P.pl_val32 = H.pl_val32;
+    P.pl_val64 = H.pl_val64;
+    P.e_s = H.e_s;
+    P.e_p = H.e_p;
+    P.n_sys = (int)n_sys;
+    P.P = Pn;
+    P.sys = d_sys;
+    P.nodes = d_nodes;
+    P.z = d_z;
+    P.tol = o.tol;
+    P.maxit = o.maxit;
+    P.reliable_every = o.reliable_every;
+    P.reliable_delta = o.reliable_delta;
+    P.timeout_ns = o.timeout_s > 0 ? (unsigned long long)(o.timeout_s * 1e9) : 0ULL;
+    P.scratch = slots;
+    P.slot_bytes = slot;
+    P.n_max = (int)((n_max + 63) / 64 * 64);
+    P.ckpt = nullptr;
+    P.ckpt_sys_off = nullptr;
+    P.work_counter = d_counter;
+    P.x_src = d_xsrc;
+    P.status = d_status;
+    P.iters = d_iters;
+    P.resid = d_resid;
+    P.n_rel = d_nrel;
+    // one CTA of 1024 threads per SM, as many as the slots in the array allow
+    const long long max_slots = (long long)(kNaScratchBytes / slot);
+    const int grid = (int)std::min<long long>(std::min<long long>(n_sm, max_slots), n_sys);
+    e = launch_cocg(P, o.precision, grid, 1024, stream);
+    if (e == cudaSuccess) e = launch_accumulate((int)nn, Pn, d_xsrc, d_z, d_w, H.dV, rho_out, e_out, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g_na_status, d_status, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g_na_iters, d_iters, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g_na_nrel, d_nrel, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g_na_resid, d_resid, n_sys * sizeof(double), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    md_stats sst;
+    std::memset(&sst, 0, sizeof(sst));
+    sst.n_systems = n_sys;
+    sst.iters_min = 1 << 30;
+    bool invalid = false;
+    for (long long k = 0; k < n_sys; ++k) {
+        const int s = g_na_status[k];
+        if (s == 0) sst.n_converged++;
+        else if (s == 2) sst.n_noconv++;
+        else if (s == 3) sst.n_breakdown++;
+        else if (s == 4) sst.n_timeout++;
+        else if (s == 1) invalid = true;
+        sst.iters_min = std::min(sst.iters_min, g_na_iters[k]);
+        sst.iters_max = std::max(sst.iters_max, g_na_iters[k]);
+        sst.total_iters += g_na_iters[k];
+        sst.total_point_iters += (long long)g_na_iters[k] * g_na_points[k / Pn];
+        sst.reliable_updates += g_na_nrel[k];
+        sst.max_resid = std::max(sst.max_resid, g_na_resid[k]);
+    }
+    sst.iters_mean = (double)sst.total_iters / (double)n_sys;
+    if (stats) *stats = sst;
+    if (invalid)
+        return set_error(MD_ERR_INVALID, "a region meets more projector atoms than the solver holds (256)");
+    if (sst.n_timeout) return set_error(MD_ERR_TIMEOUT, "device time budget exhausted; outputs incomplete");
+    if (sst.n_breakdown) return set_error(MD_ERR_BREAKDOWN, "COCG breakdown (r^T r ~ 0) in some systems");
+    if (sst.n_noconv) return set_error(MD_ERR_NOCONV, "some systems reached maxit");
+    return MD_OK;
+}
 
 using namespace md;
 
