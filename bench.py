@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--maxit", type=int, default=0, help="iteration cap (profiling runs)")
     return ap.parse_args()
 
 
@@ -210,7 +211,7 @@ def main():
     n_nodes = len(w.nodes)
     bs = min(args.nodes_per_step, n_nodes)
     n_batches = max(1, n_nodes // bs)
-    opts = SolverOptions(tol=w.tol, maxit=w.maxit, precision=prec, block=args.block,
+    opts = SolverOptions(tol=w.tol, maxit=args.maxit or w.maxit, precision=prec, block=args.block,
                          ctas_per_sm=args.ctas_per_sm)
     stream = torch.cuda.current_stream()
 
