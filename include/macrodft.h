@@ -109,14 +109,17 @@ typedef struct {
     int32_t maxit;         /* iteration cap per system, > 0 */
     int32_t precision;     /* md_precision */
     int32_t reliable_every;/* mixed: max iterations between FP64 residual
-                              recomputations (0 = 200) */
+                              recomputations (0 = 300) */
     double reliable_delta; /* mixed: also recompute when ||r|| fell by this
-                              factor since the last one (0 = 1e-2); a refresh
+                              factor since the last one (0 = 3e-3); a refresh
                               that finds the residual larger than at the
                               previous one restarts the Krylov recurrence */
     double timeout_s;      /* device wall-clock budget for the call, 0 = none */
-    int32_t block;         /* threads per CTA; 0 = library choice */
+    int32_t block;         /* threads per CTA; 0 = library choice (autotuned) */
     int32_t ctas_per_sm;   /* resident CTAs per SM; 0 = library choice */
+    int32_t kernel;        /* with block > 0: 0 or 1 = generic kernel, 2 = shared-memory
+                              z-march kernel (mixed precision, 4th/8th order, no
+                              whole-axis rings; ceil(m0*m1/block) <= 4) */
 } md_solver_opts;
 
 /* Per-call statistics, filled (after a stream synchronisation) when the

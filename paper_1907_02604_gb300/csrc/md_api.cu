@@ -177,8 +177,8 @@ md_solver_opts normalise_opts(const md_solver_opts* o) {
     md_solver_opts r;
     std::memset(&r, 0, sizeof(r));
     if (o) r = *o;
-    if (r.reliable_every <= 0) r.reliable_every = 200;
-    if (!(r.reliable_delta > 0.0)) r.reliable_delta = 1e-2;
+    if (r.reliable_every <= 0) r.reliable_every = 300;
+    if (!(r.reliable_delta > 0.0)) r.reliable_delta = 3e-3;
     return r;
 }
 
@@ -190,6 +190,7 @@ md_status check_opts(const md_solver_opts* o) {
         return set_error(MD_ERR_INVALID, "opts: unknown precision");
     if (o->block != 0 && (o->block < 64 || o->block > 1024 || o->block % 32))
         return set_error(MD_ERR_INVALID, "opts: block must be a multiple of 32 in [64, 1024]");
+    if (o->kernel < 0 || o->kernel > 2) return set_error(MD_ERR_INVALID, "opts: kernel must be 0, 1 or 2");
     return MD_OK;
 }
 
@@ -511,6 +512,8 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
 
     const int max_plane = R.max_dim[0] * R.max_dim[1];
     const bool zm_ok = zm_supported(opts.precision, H.q) && !R.any_ring;
+    P.zm_m0 = R.max_dim[0];
+    P.zm_m1 = R.max_dim[1];
     if (zm_ok) pl->smem = zm_smem_bytes(H.q, R.max_dim[0], R.max_dim[1]);
     // scratch sized for the widest candidate (2 CTAs per SM)
     const int max_ctas = (int)std::min<long long>((long long)n_sm * 2, n_sys);
@@ -530,6 +533,15 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     P.scratch = (char*)pl->scratch;
 
     Shape shape{0, opts.block > 0 ? opts.block : 512, opts.ctas_per_sm > 0 ? opts.ctas_per_sm : 0};
+    if (opts.block > 0 && opts.kernel == 2) {
+        const int K = (max_plane + opts.block - 1) / opts.block;
+        if (!zm_ok || K < 1 || K > 4 || opts.block > zm_max_threads(K))
+            return fail(set_error(MD_ERR_INVALID,
+                                  "opts: the z-march kernel needs mixed precision, 4th or 8th order, no "
+                                  "whole-axis rings and block >= m0*m1/4 within its thread limit"));
+        shape.variant = K;
+        if (shape.per_sm <= 0) shape.per_sm = 1;
+    }
     if (opts.block <= 0) {
         const std::vector<Shape> cands = candidate_shapes(pl, zm_ok, max_plane);
         md_status ts = autotune(pl, n_sm, cands, need, shape);
@@ -589,7 +601,7 @@ md_status plan_stats(md_plan* pl, cudaStream_t stream, md_stats* stats) {
     PLAN_TRY(cudaEventElapsedTime(&ms, pl->ev0, pl->ev1));
     sst.n_systems = n_sys;
     sst.iters_min = 1 << 30;
-    bool invalid = false;
+    bool invalid = false, staging_failed = false;
     for (long long k = 0; k < n_sys; ++k) {
         const int s = h_status[k];
         if (s == 0) sst.n_converged++;
@@ -597,6 +609,7 @@ md_status plan_stats(md_plan* pl, cudaStream_t stream, md_stats* stats) {
         else if (s == 3) sst.n_breakdown++;
         else if (s == 4) sst.n_timeout++;
         else if (s == 1) invalid = true;
+        else if (s == 5) staging_failed = true;
         sst.iters_min = std::min(sst.iters_min, h_iters[k]);
         sst.iters_max = std::max(sst.iters_max, h_iters[k]);
         sst.total_iters += h_iters[k];
@@ -607,6 +620,8 @@ md_status plan_stats(md_plan* pl, cudaStream_t stream, md_stats* stats) {
     sst.iters_mean = (double)sst.total_iters / (double)n_sys;
     sst.kernel_ms = ms;
     if (stats) *stats = sst;
+    if (staging_failed)
+        return set_error(MD_ERR_CUDA, "a shared-memory staging copy did not complete in time");
     if (invalid)
         return set_error(MD_ERR_INVALID, "a region meets more projector atoms than the solver holds (256)");
     if (sst.n_timeout) return set_error(MD_ERR_TIMEOUT, "device time budget exhausted; outputs incomplete");

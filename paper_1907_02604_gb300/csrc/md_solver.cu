@@ -145,6 +145,8 @@ struct Shared {
     short la_off[kLocal][3];
     double2 c[kLocal][4];   // E_l dV C_l sum_i f_l(i) v(i), double
     double2 pnl[32];        // per warp: sum over its atoms of E_l dV c_l^2 (v^T V_nl v)
+    float cacc[kLocal][8];  // z-march: raw projections sum_i f_l(i) v(i), accumulated per plane
+    uint64_t bar[4];        // z-march: staging-slot mbarriers
     float2 cf[kLocal][4];   // the same rounded to float
     short map[kMapMax];     // global atom id -> local slot, -1 if absent
 };
@@ -872,60 +874,145 @@ __global__ void k_accumulate(int n_nodes, int Pn, const double2* __restrict__ x_
 }
 
 
-// Nonlocal part of (H_R v)(i) from the coefficients in S.cf (mixed path).
-__device__ __forceinline__ float2 nl_apply(const SolveParams& P, const Geo& G, const Shared& S, int i) {
-    const int c = (int)fdiv((uint32_t)i, G.div_plane);
-    const int rem = i - c * G.plane;
-    const int b = (int)fdiv((uint32_t)rem, G.div_row);
-    const int a = rem - b * G.m[0];
-    const int gx = wrap_once(G.lo[0] + a, P.n[0]);
-    const int gy = wrap_once(G.lo[1] + b, P.n[1]);
-    const int gz = wrap_once(G.lo[2] + c, P.n[2]);
-    const long long gi = gx + (long long)P.n[0] * (gy + (long long)P.n[1] * gz);
-    float yx = 0.f, yy = 0.f;
-    const int e0 = __ldg(P.pl_ptr + gi), e1 = __ldg(P.pl_ptr + gi + 1);
-    for (int e = e0; e < e1; ++e) {
-        const int k = local_slot(P, S, __ldg(P.pl_atom + e));
-        if (k < 0) continue;
-        const float4 f = __ldg(P.pl_val32 + e);
-        const float2 c0 = S.cf[k][0], c1 = S.cf[k][1], c2 = S.cf[k][2], c3 = S.cf[k][3];
-        yx += f.x * c0.x + f.y * c1.x + f.z * c2.x + f.w * c3.x;
-        yy += f.x * c0.y + f.y * c1.y + f.z * c2.y + f.w * c3.y;
-    }
-    return make_float2(yx, yy);
-}
-
 template <int K>
 struct ZmThreads {
     static constexpr int value = K == 1 ? 1024 : (K == 2 ? 576 : (K == 3 ? 384 : 288));
 };
 
+constexpr int kStages = 4;               // staging slots: planes prefetched 3 ahead
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+// Dynamic shared memory of the z-march kernel for launch-wide maximal
+// region extents M0 x M1 (the same arithmetic on host and device).
+struct ZmLayout {
+    size_t plane_off, nl_off, stage_off, stage_bytes, total;
+    __host__ __device__ ZmLayout(int q, int M0, int M1) {
+        const size_t pb = (size_t)(M0 + 2 * q) * (size_t)(M1 + 2 * q);   // bordered plane
+        const size_t pl = (size_t)M0 * (size_t)M1;
+        plane_off = 0;
+        nl_off = plane_off + 2 * pb * sizeof(float2);
+        stage_bytes = (pl * sizeof(float2) + 16 + 15) / 16 * 16;          // one staged plane
+        stage_off = (nl_off + 2 * pl * sizeof(float2) + 127) / 128 * 128;
+        total = stage_off + (size_t)kStages * 2 * stage_bytes;
+    }
+};
+
+// Window index of region slot c for an atom window starting at region
+// offset off (inverse of region_slot); -1 if the window misses it.
+__device__ __forceinline__ int window_index(int off, int c, int n, int len, int periodic) {
+    int w = c - off;
+    if (periodic && w < 0) w += n;
+    return (w >= 0 && w < len) ? w : -1;
+}
+
+// Issue the bulk copies of plane `cn` of r and p into staging slot cn % kStages.
+__device__ __forceinline__ void zm_issue(const SolveParams& P, const Geo& G, unsigned char* stage,
+                                         size_t stage_bytes, uint64_t* bars, const float2* r,
+                                         const float2* p, int cn) {
+    const int slot = cn % kStages;
+    const uintptr_t sr = (uintptr_t)(r + (size_t)cn * G.plane);
+    const uintptr_t sp = (uintptr_t)(p + (size_t)cn * G.plane);
+    const uintptr_t ar = sr & ~(uintptr_t)15, ap = sp & ~(uintptr_t)15;
+    const uint32_t br = (uint32_t)(((sr + (uintptr_t)G.plane * 8 + 15) & ~(uintptr_t)15) - ar);
+    const uint32_t bp = (uint32_t)(((sp + (uintptr_t)G.plane * 8 + 15) & ~(uintptr_t)15) - ap);
+    unsigned char* dst = stage + (size_t)slot * 2 * stage_bytes;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&bars[slot], br + bp);
+    bulk_copy_g2s(dst, (const void*)ar, br, &bars[slot]);
+    bulk_copy_g2s(dst + stage_bytes, (const void*)ap, bp, &bars[slot]);
+}
+
+// Projections of the published plane c (bordered buffer, row pitch `pitch`,
+// border width q) onto the local projectors, added into S.cacc: warp per
+// local atom, lane per row of the disk where its sphere cuts the plane.
+__device__ __noinline__ void zm_nl_dot_plane(const SolveParams& P, const Geo& G, Shared& S,
+                                             const float2* __restrict__ buf, int pitch, int Q, int c) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int m0 = G.m[0], m1 = G.m[1];
+            for (int kk = warp; kk < S.n_local; kk += nw) {
+                const int at = S.la_id[kk];
+                const int lz = __ldg(P.proj_len + 3 * at + 2);
+                const int ww = window_index(S.la_off[kk][2], c, P.n[2], lz, P.periodic[2]);
+                if (ww < 0) continue;
+                const int lx = __ldg(P.proj_len + 3 * at), ly = __ldg(P.proj_len + 3 * at + 1);
+                const float* dxt = P.proj_d32 + (3LL * at + 0) * kMaxProjWin;
+                const float* gxt = P.proj_g32 + (3LL * at + 0) * kMaxProjWin;
+                const Runs rx = axis_runs(S.la_off[kk][0], lx, P.n[0], m0, P.periodic[0]);
+                const unsigned char* rows = P.proj_rows + 2 * (((long long)at * kMaxProjWin + ww) * kMaxProjWin);
+                const float gz = __ldg(P.proj_g32 + (3LL * at + 2) * kMaxProjWin + ww);
+                const float dz = __ldg(P.proj_d32 + (3LL * at + 2) * kMaxProjWin + ww);
+                float acc8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                for (int vv2 = lane; vv2 < ly; vv2 += 32) {
+                    const int b = region_slot(S.la_off[kk][1], vv2, P.n[1], m1, P.periodic[1]);
+                    if (b < 0) continue;
+                    const int u0 = rows[2 * vv2], u1 = rows[2 * vv2 + 1];
+                    const float2* brow = buf + (b + Q) * pitch + Q;
+                    float Ar = 0.f, Ai = 0.f, Br = 0.f, Bi = 0.f;
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const int lo = max(u0, rx.lo[t]), hi = min(u1, rx.hi[t]);
+                        for (int u = lo; u <= hi; ++u) {
+                            const float2 pv = brow[u + rx.shift[t]];
+                            const float g1 = __ldg(gxt + u);
+                            const float g2 = __ldg(dxt + u) * g1;
+                            Ar += g1 * pv.x; Ai += g1 * pv.y;
+                            Br += g2 * pv.x; Bi += g2 * pv.y;
+                        }
+                    }
+                    const float gyz = __ldg(P.proj_g32 + (3LL * at + 1) * kMaxProjWin + vv2) * gz;
+                    const float ey = __ldg(P.proj_d32 + (3LL * at + 1) * kMaxProjWin + vv2) * gyz;
+                    const float ez = dz * gyz;
+                    acc8[0] += gyz * Ar; acc8[1] += gyz * Ai;
+                    acc8[2] += gyz * Br; acc8[3] += gyz * Bi;
+                    acc8[4] += ey * Ar;  acc8[5] += ey * Ai;
+                    acc8[6] += ez * Ar;  acc8[7] += ez * Ai;
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float v = warp_sum(acc8[t]);
+                    if (lane == 0) atomicAdd(&S.cacc[kk][t], v);
+                }
+            }
+        }
+
 // Fused P1 + local P2 of the mixed iteration, staged through shared memory.
 // Each thread owns K (x, y) columns of the region and walks z; the 2Q+1
 // values of p_new along a column sit in registers (the z part of the
 // stencil), and the current plane is published in a zero-bordered buffer
-// of (m0 + 2Q) x (m1 + 2Q) points for the x and y neighbours.  Two buffers
-// alternate, so one barrier per plane suffices.  p_new = r + beta p_old is
-// formed once as a value enters the window and written back to global
-// memory; the next plane's r and p_old and this plane's V are loaded one
-// step ahead.  Outputs: p (new), Ap_loc = (-1/2 L + V - z) p, and the
-// thread's partial of p^T Ap_loc.
+// for the x and y neighbours (two buffers alternate: one barrier per
+// plane).  The r and p_old planes the window needs next arrive by bulk
+// asynchronous copies three planes ahead (mbarrier completion), so HBM
+// latency is off the critical path.  While a plane is published, warps
+// also accumulate the nonlocal coefficients c_al over the disk where each
+// local atom's projector sphere cuts that plane (separable Gaussian: per
+// row A = sum g_x v, B = sum d_x g_x v).  Outputs: p (new), Ap_loc =
+// (-1/2 L + V - z) p, S.cacc (raw projections), the thread's p^T Ap_loc.
 template <int Q, int K>
-__device__ __forceinline__ void zm_stencil_pass(const SolveParams& P, const Geo& G, const Shared& S,
-                                                float2* __restrict__ sbuf, const float2* __restrict__ r,
-                                                float2* __restrict__ p, float2* __restrict__ Ap,
-                                                float br, float bi, float zr, float zi, float diag,
-                                                KSum<float>& acc_re, KSum<float>& acc_im) {
+__device__ __forceinline__ void zm_stencil_pass(const SolveParams& P, const Geo& G, Shared& S,
+                                                unsigned char* dsm, const ZmLayout& L, uint32_t& ph,
+                                                const float2* __restrict__ r, float2* __restrict__ p,
+                                                float2* __restrict__ Ap, float br, float bi, float zr,
+                                                float zi, float diag, KSum<float>& acc_re,
+                                                KSum<float>& acc_im) {
     const int T = blockDim.x;
     const int m0 = G.m[0], m1 = G.m[1], m2 = G.m[2], plane = G.plane;
     const int pitch = m0 + 2 * Q;
     const int bufsz = pitch * (m1 + 2 * Q);
     const long long nxy = (long long)P.n[0] * P.n[1];
     const float* cf = coef_of<float>(S);
+    float2* pbuf = reinterpret_cast<float2*>(dsm + L.plane_off);
+    unsigned char* stage = dsm + L.stage_off;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+    // staging offset (elements) of the plane start inside a 16-byte aligned copy
+    const int soff = (int)((((uintptr_t)r) & 15) / 8);   // r and p share the residue per plane parity
     int col[K], sidx[K];
     long long vbase[K];
     bool ok[K];
     float2 win[K][2 * Q + 1];
+    if (P.nonlocal)
+        for (int t = threadIdx.x; t < S.n_local * 8; t += T) (&S.cacc[0][0])[t] = 0.f;
+    if (threadIdx.x == 0)
+        for (int cn = Q + 1; cn < m2 && cn <= Q + kStages - 1; ++cn) zm_issue(P, G, stage, L.stage_bytes, S.bar, r, p, cn);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         col[k] = threadIdx.x + k * T;
@@ -949,11 +1036,20 @@ __device__ __forceinline__ void zm_stencil_pass(const SolveParams& P, const Geo&
         }
     }
     for (int c = 0; c < m2; ++c) {
-        float2* buf = sbuf + (c & 1) * bufsz;
+        float2* buf = pbuf + (c & 1) * bufsz;
         const int cn = c + Q + 1;
         const long long voff = nxy * wrap_once(G.lo[2] + c, P.n[2]);
         float2 nr[K], np[K];
         float vv[K];
+        if (cn < m2) {
+            const int slot = cn % kStages;
+            if (!mbar_wait_bounded(&S.bar[slot], (ph >> slot) & 1u, kWaitLimit)) S.flag = 2;
+            ph ^= 1u << slot;
+        }
+        const float2* sr = reinterpret_cast<const float2*>(stage + (size_t)(cn % kStages) * 2 * L.stage_bytes);
+        const float2* sp = reinterpret_cast<const float2*>(stage + (size_t)(cn % kStages) * 2 * L.stage_bytes +
+                                                           L.stage_bytes);
+        const int so = (int)(((((uintptr_t)r) + (uintptr_t)cn * plane * 8) & 15) / 8);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             nr[k] = make_float2(0.f, 0.f);
@@ -962,13 +1058,15 @@ __device__ __forceinline__ void zm_stencil_pass(const SolveParams& P, const Geo&
             if (ok[k]) {
                 vv[k] = __ldg(P.V32 + vbase[k] + voff);
                 if (cn < m2) {
-                    nr[k] = r[col[k] + cn * plane];
-                    np[k] = p[col[k] + cn * plane];
+                    nr[k] = sr[so + col[k]];
+                    np[k] = sp[so + col[k]];
                 }
                 buf[sidx[k]] = win[k][Q];
             }
         }
         __syncthreads();
+        if (threadIdx.x == 0 && cn + kStages - 1 < m2)
+            zm_issue(P, G, stage, L.stage_bytes, S.bar, r, p, cn + kStages - 1);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             if (ok[k]) {
@@ -990,6 +1088,10 @@ __device__ __forceinline__ void zm_stencil_pass(const SolveParams& P, const Geo&
                 acc_re.add(ctr.x * yx - ctr.y * yy);
                 acc_im.add(ctr.x * yy + ctr.y * yx);
             }
+        }
+        if (P.nonlocal) zm_nl_dot_plane(P, G, S, buf, pitch, Q, c);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
 #pragma unroll
             for (int t = 0; t < 2 * Q; ++t) win[k][t] = win[k][t + 1];
             float2 v = make_float2(0.f, 0.f);
@@ -1000,6 +1102,55 @@ __device__ __forceinline__ void zm_stencil_pass(const SolveParams& P, const Geo&
             win[k][2 * Q] = v;
         }
     }
+    (void)soff;
+}
+
+// Nonlocal contribution of plane c, accumulated atom by atom into the plane
+// buffer nl (m0 x m1, shared memory) with shared-memory atomics:
+//   nl(i) += sum_l C_l f_l(i) (E_l dV c_al),  f = (1, d_x, d_y, d_z) g_x g_y g_z.
+__device__ __noinline__ void zm_nl_plane(const SolveParams& P, const Geo& G, const Shared& S,
+                                            float2* nl, int c) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int m0 = G.m[0], m1 = G.m[1];
+    for (int kk = warp; kk < S.n_local; kk += nw) {
+        const int at = S.la_id[kk];
+        const int lz = __ldg(P.proj_len + 3 * at + 2);
+        const int ww = window_index(S.la_off[kk][2], c, P.n[2], lz, P.periodic[2]);
+        if (ww < 0) continue;
+        const int lx = __ldg(P.proj_len + 3 * at), ly = __ldg(P.proj_len + 3 * at + 1);
+        const float* dxt = P.proj_d32 + (3LL * at + 0) * kMaxProjWin;
+        const float* gxt = P.proj_g32 + (3LL * at + 0) * kMaxProjWin;
+        const Runs rx = axis_runs(S.la_off[kk][0], lx, P.n[0], m0, P.periodic[0]);
+        const unsigned char* rows = P.proj_rows + 2 * (((long long)at * kMaxProjWin + ww) * kMaxProjWin);
+        const float gz = __ldg(P.proj_g32 + (3LL * at + 2) * kMaxProjWin + ww);
+        const float dz = __ldg(P.proj_d32 + (3LL * at + 2) * kMaxProjWin + ww);
+        const float C0 = __ldg(P.proj_C32 + 4LL * at), C1 = __ldg(P.proj_C32 + 4LL * at + 1),
+                    C2 = __ldg(P.proj_C32 + 4LL * at + 2), C3 = __ldg(P.proj_C32 + 4LL * at + 3);
+        const float2 c0 = S.cf[kk][0], c1 = S.cf[kk][1], c2 = S.cf[kk][2], c3 = S.cf[kk][3];
+        // per-atom constant parts: K1 = C_s c_s + d_y C_y c_y + d_z C_z c_z (row-wise), K2 = C_x c_x
+        for (int vv2 = lane; vv2 < ly; vv2 += 32) {
+            const int b = region_slot(S.la_off[kk][1], vv2, P.n[1], m1, P.periodic[1]);
+            if (b < 0) continue;
+            const int u0 = rows[2 * vv2], u1 = rows[2 * vv2 + 1];
+            const float gyz = __ldg(P.proj_g32 + (3LL * at + 1) * kMaxProjWin + vv2) * gz;
+            const float dy = __ldg(P.proj_d32 + (3LL * at + 1) * kMaxProjWin + vv2);
+            const float k1r = gyz * (C0 * c0.x + dy * C2 * c2.x + dz * C3 * c3.x);
+            const float k1i = gyz * (C0 * c0.y + dy * C2 * c2.y + dz * C3 * c3.y);
+            const float k2r = gyz * C1 * c1.x, k2i = gyz * C1 * c1.y;
+            float2* nrow = nl + b * m0;
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int lo = max(u0, rx.lo[t]), hi = min(u1, rx.hi[t]);
+                for (int u = lo; u <= hi; ++u) {
+                    const float g1 = __ldg(gxt + u);
+                    const float g2 = __ldg(dxt + u) * g1;
+                    float2* dst = nrow + u + rx.shift[t];
+                    atomicAdd(&dst->x, g1 * k1r + g2 * k2r);
+                    atomicAdd(&dst->y, g1 * k1i + g2 * k2i);
+                }
+            }
+        }
+    }
 }
 
 // Mixed-precision persistent COCG with the shared-memory z-march stencil
@@ -1007,13 +1158,14 @@ __device__ __forceinline__ void zm_stencil_pass(const SolveParams& P, const Geo&
 // thread, blockDim.x * K >= m0 * m1 for every region of the launch).
 // The nonlocal term enters through the bilinear identity
 //   p^T A p = p^T A_loc p + sum_al E_l dV c_al^2
-// (c from the warp-per-atom dot) and is applied to Ap pointwise in P3.
+// and is added to Ap plane by plane in P3 from a shared-memory buffer.
 template <int Q, int K>
 __global__ void __launch_bounds__(ZmThreads<K>::value) k_cocg_zm(const __grid_constant__ SolveParams P) {
     using Mode = MixedModeT;
     using C = float2;
     __shared__ Shared S;
-    extern __shared__ float2 sbuf[];
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const ZmLayout L(Q, P.zm_m0, P.zm_m1);
     const uint64_t t_start = global_time_ns();
     char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
     for (int t = threadIdx.x; t < 3 * kMaxQ; t += blockDim.x) {
@@ -1023,7 +1175,14 @@ __global__ void __launch_bounds__(ZmThreads<K>::value) k_cocg_zm(const __grid_co
     if (P.nonlocal && P.n_atoms <= kMapMax)
         for (int t = threadIdx.x; t < P.n_atoms; t += blockDim.x) S.map[t] = -1;
     if (threadIdx.x < 32) S.pnl[threadIdx.x] = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kStages; ++k) mbar_init(&S.bar[k], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    uint32_t ph = 0;   // parity of the next wait on each staging slot
     const float diagF = (float)P.diag;
+    float2* nlbuf = reinterpret_cast<float2*>(dsm + L.nl_off);
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1059,9 +1218,11 @@ __global__ void __launch_bounds__(ZmThreads<K>::value) k_cocg_zm(const __grid_co
         if (P.ckpt) x = P.ckpt + P.ckpt_sys_off[out_idx];
 
         if (P.nonlocal) collect_local_atoms(P, G, S);
-        {   // zero both plane buffers (their borders stay zero)
+        {   // zero the bordered plane buffers (borders stay zero) and the nonlocal planes
             const int bufsz = (G.m[0] + 2 * Q) * (G.m[1] + 2 * Q);
-            for (int t = threadIdx.x; t < 2 * bufsz; t += blockDim.x) sbuf[t] = make_float2(0.f, 0.f);
+            float2* pb = reinterpret_cast<float2*>(dsm + L.plane_off);
+            for (int t = threadIdx.x; t < 2 * bufsz; t += blockDim.x) pb[t] = make_float2(0.f, 0.f);
+            for (int t = threadIdx.x; t < 2 * G.plane; t += blockDim.x) nlbuf[t] = make_float2(0.f, 0.f);
         }
         for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
             r[i] = make_float2(i == G.src ? 1.f : 0.f, 0.f);
@@ -1092,24 +1253,32 @@ __global__ void __launch_bounds__(ZmThreads<K>::value) k_cocg_zm(const __grid_co
             __syncthreads();
             if (S.action == kStop || S.action == kStopTimeout) break;
             KSum<float> acc_re, acc_im;
-            zm_stencil_pass<Q, K>(P, G, S, sbuf, r, p, Ap, (float)S.beta[0], (float)S.beta[1], zr, zi,
+            zm_stencil_pass<Q, K>(P, G, S, dsm, L, ph, r, p, Ap, (float)S.beta[0], (float)S.beta[1], zr, zi,
                                   diagF, acc_re, acc_im);
             __syncthreads();
-            if (P.nonlocal) nonlocal_coeffs<float, float2>(P, G, S, p);
-            {
-                float hi[2] = {acc_re.hi(), acc_im.hi()}, lo[2] = {acc_re.lo(), acc_im.lo()};
-                if (P.nonlocal && (threadIdx.x & 31) == 0) {
-                    const double2 q = S.pnl[threadIdx.x >> 5];
-                    const float qr = (float)q.x, qi = (float)q.y;
-                    ff_add(hi[0], lo[0], qr, (float)(q.x - (double)qr));
-                    ff_add(hi[1], lo[1], qi, (float)(q.y - (double)qi));
+            float hi[2] = {acc_re.hi(), acc_im.hi()}, lo[2] = {acc_re.lo(), acc_im.lo()};
+            if (P.nonlocal) {
+                // coefficients E_l dV C_l s_l and the bilinear energy E_l dV (C_l s_l)^2
+                for (int t = threadIdx.x; t < S.n_local * 4; t += blockDim.x) {
+                    const int kk = t >> 2, l = t & 3;
+                    const double sr = S.cacc[kk][2 * l], si = S.cacc[kk][2 * l + 1];
+                    const double Cl = __ldg(P.proj_C + 4LL * S.la_id[kk] + l);
+                    const double E = (l == 0 ? P.e_s : P.e_p) * P.dV * Cl;
+                    S.c[kk][l] = make_double2(E * sr, E * si);
+                    S.cf[kk][l] = make_float2((float)(E * sr), (float)(E * si));
+                    const double er = E * Cl * (sr * sr - si * si), ei = E * Cl * 2.0 * sr * si;
+                    const float qr = (float)er, qi = (float)ei;
+                    ff_add(hi[0], lo[0], qr, (float)(er - (double)qr));
+                    ff_add(hi[1], lo[1], qi, (float)(ei - (double)qi));
                 }
+            }
+            {
                 double pap[2];
                 block_reduce_ff<2>(S, hi, lo, pap);
                 if (threadIdx.x == 0) {
                     ++S.it;
                     const double den = pap[0] * pap[0] + pap[1] * pap[1];
-                    if (!(den > 0.0)) {
+                    if (S.flag == 2 || !(den > 0.0)) {
                         S.st = 3;
                         S.action = kStop;
                     } else {
@@ -1121,55 +1290,39 @@ __global__ void __launch_bounds__(ZmThreads<K>::value) k_cocg_zm(const __grid_co
                 if (S.action == kStop) break;
             }
             double red3[3];
-            {   // P3: dx += alpha p ; r -= alpha (Ap_loc + Ap_nl) ; r^T r ; |r|^2
+            {   // P3, plane by plane: dx += alpha p ; r -= alpha (Ap_loc + Ap_nl) ; dots
                 const float ar = (float)S.alpha[0], ai = (float)S.alpha[1];
                 KSum<float> s_re, s_im, s_n;
-                const float4* p4 = reinterpret_cast<const float4*>(p);
-                const float4* q4 = reinterpret_cast<const float4*>(Ap);
-                float4* d4 = reinterpret_cast<float4*>(dx);
-                float4* r4 = reinterpret_cast<float4*>(r);
-                const int npair = G.n >> 1;
-                for (int k = threadIdx.x; k < npair; k += blockDim.x) {
-                    const float4 pv = p4[k];
-                    float4 qv = q4[k];
-                    if (P.nonlocal) {
-                        const float2 n0 = nl_apply(P, G, S, 2 * k), n1 = nl_apply(P, G, S, 2 * k + 1);
-                        qv.x += n0.x; qv.y += n0.y; qv.z += n1.x; qv.w += n1.y;
-                    }
-                    float4 d = d4[k], rv = r4[k];
-                    d.x += ar * pv.x - ai * pv.y;
-                    d.y += ar * pv.y + ai * pv.x;
-                    d.z += ar * pv.z - ai * pv.w;
-                    d.w += ar * pv.w + ai * pv.z;
-                    rv.x -= ar * qv.x - ai * qv.y;
-                    rv.y -= ar * qv.y + ai * qv.x;
-                    rv.z -= ar * qv.z - ai * qv.w;
-                    rv.w -= ar * qv.w + ai * qv.z;
-                    d4[k] = d;
-                    r4[k] = rv;
-                    s_re.add(rv.x * rv.x - rv.y * rv.y + (rv.z * rv.z - rv.w * rv.w));
-                    s_im.add(2.f * (rv.x * rv.y + rv.z * rv.w));
-                    s_n.add(rv.x * rv.x + rv.y * rv.y + (rv.z * rv.z + rv.w * rv.w));
+                const int plane = G.plane, m2 = G.m[2];
+                if (P.nonlocal) {
+                    zm_nl_plane(P, G, S, nlbuf, 0);
+                    __syncthreads();
                 }
-                if ((G.n & 1) && threadIdx.x == 0) {
-                    const int i = G.n - 1;
-                    const C pi = p[i];
-                    C api = Ap[i];
-                    if (P.nonlocal) {
-                        const float2 n0 = nl_apply(P, G, S, i);
-                        api.x += n0.x;
-                        api.y += n0.y;
+                for (int c = 0; c < m2; ++c) {
+                    float2* nlc = nlbuf + (c & 1) * plane;
+                    if (P.nonlocal && c + 1 < m2) zm_nl_plane(P, G, S, nlbuf + ((c + 1) & 1) * plane, c + 1);
+                    for (int col = threadIdx.x; col < plane; col += blockDim.x) {
+                        const int i = col + c * plane;
+                        const float2 pv = p[i];
+                        float2 qv = Ap[i];
+                        if (P.nonlocal) {
+                            const float2 nv = nlc[col];
+                            qv.x += nv.x;
+                            qv.y += nv.y;
+                            nlc[col] = make_float2(0.f, 0.f);
+                        }
+                        float2 d = dx[i], rv = r[i];
+                        d.x += ar * pv.x - ai * pv.y;
+                        d.y += ar * pv.y + ai * pv.x;
+                        rv.x -= ar * qv.x - ai * qv.y;
+                        rv.y -= ar * qv.y + ai * qv.x;
+                        dx[i] = d;
+                        r[i] = rv;
+                        s_re.add(rv.x * rv.x - rv.y * rv.y);
+                        s_im.add(2.f * rv.x * rv.y);
+                        s_n.add(rv.x * rv.x + rv.y * rv.y);
                     }
-                    C d = dx[i], ri = r[i];
-                    d.x += ar * pi.x - ai * pi.y;
-                    d.y += ar * pi.y + ai * pi.x;
-                    ri.x -= ar * api.x - ai * api.y;
-                    ri.y -= ar * api.y + ai * api.x;
-                    dx[i] = d;
-                    r[i] = ri;
-                    s_re.add(ri.x * ri.x - ri.y * ri.y);
-                    s_im.add(2.f * ri.x * ri.y);
-                    s_n.add(ri.x * ri.x + ri.y * ri.y);
+                    if (P.nonlocal) __syncthreads();
                 }
                 const float hi3[3] = {s_re.hi(), s_im.hi(), s_n.hi()};
                 const float lo3[3] = {s_re.lo(), s_im.lo(), s_n.lo()};
@@ -1230,7 +1383,7 @@ __global__ void __launch_bounds__(ZmThreads<K>::value) k_cocg_zm(const __grid_co
         __syncthreads();
         if (threadIdx.x == 0) {
             P.x_src[out_idx] = x[G.src];
-            P.status[out_idx] = timed_out ? 4 : (S.flag ? 1 : status);
+            P.status[out_idx] = timed_out ? 4 : (S.flag == 2 ? 5 : (S.flag ? 1 : status));
             P.iters[out_idx] = S.it;
             P.resid[out_idx] = S.rn;
             P.n_rel[out_idx] = S.n_rel;
@@ -1267,7 +1420,7 @@ template <int Q, int K>
 cudaError_t launch_zm_k(const SolveParams& P, int grid, int block, size_t smem, cudaStream_t stream) {
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_cocg_zm<Q, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaFuncSetAttribute(k_cocg_zm<Q, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
         configured = true;
     }
     k_cocg_zm<Q, K><<<grid, block, smem, stream>>>(P);
@@ -1301,7 +1454,7 @@ bool zm_supported(int precision, int q) { return precision == MD_PREC_MIXED && (
 
 template <int Q, int K>
 int zm_occ_k(int block, size_t smem) {
-    cudaFuncSetAttribute(k_cocg_zm<Q, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(k_cocg_zm<Q, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cocg_zm<Q, K>, block, smem) != cudaSuccess) {
         cudaGetLastError();
@@ -1329,9 +1482,7 @@ int zm_occupancy(int q, int K, int block, size_t smem) {
     return 0;
 }
 
-size_t zm_smem_bytes(int q, int max_m0, int max_m1) {
-    return 2 * sizeof(float2) * (size_t)(max_m0 + 2 * q) * (size_t)(max_m1 + 2 * q);
-}
+size_t zm_smem_bytes(int q, int max_m0, int max_m1) { return ZmLayout(q, max_m0, max_m1).total; }
 
 cudaError_t launch_cocg_zm(const SolveParams& P, int K, int grid, int block, size_t smem, cudaStream_t stream) {
     if (P.q == 2) return launch_zm_q<2>(P, K, grid, block, smem, stream);

@@ -65,6 +65,7 @@ struct SolveParams {
     char* scratch;
     size_t slot_bytes;
     int n_max;                      // vector length per slot (rounded up)
+    int zm_m0, zm_m1;               // z-march kernel: largest region extents in x, y
     double2* ckpt;                  // NULL or checkpoint base
     const long long* ckpt_sys_off;  // point offset of system (node*P + pole) in ckpt
     unsigned int* work_counter;
