@@ -120,6 +120,14 @@ typedef struct {
     int32_t kernel;        /* with block > 0: 0 or 1 = generic kernel, 2 = shared-memory
                               z-march kernel (mixed precision, 4th/8th order, no
                               whole-axis rings; ceil(m0*m1/block) <= 4) */
+    int32_t method;        /* 0 = one COCG per (node, pole) system.
+                              1 = shifted COCG: per node one Krylov sequence, seeded
+                              with the pole nearest the real axis, serves all P poles
+                              (residuals r/pi_k; Jegerlehner 1996, Takayama et al.
+                              2006); only x_k(j) is tracked, so it gives rho and e but
+                              no checkpoint (md_density_adjoint needs method 0);
+                              P <= 64.  Matvecs per node drop from sum_k iters_k to
+                              max_k iters_k. */
 } md_solver_opts;
 
 /* Per-call statistics, filled (after a stream synchronisation) when the
@@ -272,7 +280,9 @@ md_status md_density_adjoint(const md_hamiltonian* ham, const md_poles* poles,
  * the library holds until the process exits.  It calls no cudaMalloc,
  * cudaFree or other allocating routine, and nothing on the host heap on
  * success (error messages excepted).  The Hamiltonian must be built
- * beforehand (md_build_hamiltonian allocates).
+ * beforehand (md_build_hamiltonian allocates).  It always solves one COCG
+ * per (node, pole) system on the generic kernel (opts->method, ->kernel and
+ * ->block are ignored).
  *   - Limits: n_nodes <= MD_NOALLOC_MAX_NODES, P <= MD_NOALLOC_MAX_POLES,
  *     n_nodes * P <= MD_NOALLOC_MAX_SYSTEMS, and one region's Krylov slot
  *     (48 B per point mixed, 64 B per point FP64) within

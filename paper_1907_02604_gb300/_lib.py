@@ -49,7 +49,8 @@ class md_solver_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("reliable_every", ctypes.c_int32), ("reliable_delta", ctypes.c_double),
                 ("timeout_s", ctypes.c_double), ("block", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("method", ctypes.c_int32)]
 
 
 class md_stats(ctypes.Structure):

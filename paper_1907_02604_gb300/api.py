@@ -65,13 +65,15 @@ class SolverOptions:
     block: int = 0
     ctas_per_sm: int = 0
     kernel: str = "auto"           # "auto", "generic" or "zmarch" (the last two need block > 0)
+    method: str = "cocg"           # "cocg" (one solve per pole) or "shifted" (one per node)
 
     def to_c(self) -> _lib.md_solver_opts:
         prec = {"fp64": _lib.MD_PREC_FP64, "mixed": _lib.MD_PREC_MIXED}[self.precision]
         kern = {"auto": 0, "generic": 1, "zmarch": 2}[self.kernel]
+        meth = {"cocg": 0, "shifted": 1}[self.method]
         return _lib.md_solver_opts(self.tol, self.maxit, prec, self.reliable_every,
                                    self.reliable_delta, self.timeout_s, self.block, self.ctas_per_sm,
-                                   kern)
+                                   kern, meth)
 
 
 class Hamiltonian:

@@ -191,6 +191,7 @@ md_status check_opts(const md_solver_opts* o) {
     if (o->block != 0 && (o->block < 64 || o->block > 1024 || o->block % 32))
         return set_error(MD_ERR_INVALID, "opts: block must be a multiple of 32 in [64, 1024]");
     if (o->kernel < 0 || o->kernel > 2) return set_error(MD_ERR_INVALID, "opts: kernel must be 0, 1 or 2");
+    if (o->method < 0 || o->method > 1) return set_error(MD_ERR_INVALID, "opts: method must be 0 or 1");
     return MD_OK;
 }
 
@@ -218,6 +219,7 @@ struct md_plan {
     long long n_sys = 0;
     int grid = 0, block = 0;
     int variant = 0;                   // 0 generic kernel, K > 0: z-march kernel with K columns per thread
+    bool multishift = false;           // one shifted-COCG work item per node
     size_t smem = 0;                   // dynamic shared memory of the z-march kernel
     std::vector<long long> points;     // region points per node
     md::SolveParams P;
@@ -318,16 +320,17 @@ std::vector<TuneEntry> g_tune_cache;
 md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_t scratch_bytes,
                    Shape& out) {
     const TuneKey key{pl->precision, pl->P.q, (int)((pl->P.n_max + 4095) / 4096), pl->P.nonlocal,
-                      cands.size() > 2 ? 1 : 0};
+                      (cands.size() > 2 ? 1 : 0) + 2 * pl->P.multishift};
     for (const auto& e : g_tune_cache)
         if (e.key == key) {
             out = e.shape;
             return MD_OK;
         }
-    const long long ns = std::min<long long>(pl->n_sys, n_sm);
-    std::vector<SysDesc> all(pl->n_sys), sample;
-    PLAN_TRY(cudaMemcpy(all.data(), pl->d_sys, pl->n_sys * sizeof(SysDesc), cudaMemcpyDeviceToHost));
-    for (long long k = 0; k < ns; ++k) sample.push_back(all[(k * pl->n_sys) / ns]);
+    const long long nw = pl->P.n_sys;   // work items (systems, or nodes with shifted COCG)
+    const long long ns = std::min<long long>(nw, n_sm);
+    std::vector<SysDesc> all(nw), sample;
+    PLAN_TRY(cudaMemcpy(all.data(), pl->d_sys, nw * sizeof(SysDesc), cudaMemcpyDeviceToHost));
+    for (long long k = 0; k < ns; ++k) sample.push_back(all[(k * nw) / ns]);
     SysDesc* d_sample = nullptr;
     PLAN_TRY(cudaMalloc(&d_sample, ns * sizeof(SysDesc)));
     cudaMemcpy(d_sample, sample.data(), ns * sizeof(SysDesc), cudaMemcpyHostToDevice);
@@ -358,7 +361,12 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
         cudaEventElapsedTime(&ms, pl->ev0, pl->ev1);
         cudaMemcpy(h_it.data(), T.iters, pl->n_sys * sizeof(int), cudaMemcpyDeviceToHost);
         long long pit = 0;
-        for (const auto& sd : sample) pit += (long long)h_it[(long long)sd.node * pl->Pn + sd.pole] * pl->points[sd.node];
+        for (const auto& sd : sample) {
+            int it = h_it[(long long)sd.node * pl->Pn + sd.pole];
+            if (pl->multishift)
+                for (int p = 0; p < pl->Pn; ++p) it = std::max(it, h_it[(long long)sd.node * pl->Pn + p]);
+            pit += (long long)it * pl->points[sd.node];
+        }
         const double rate = ms > 0 ? (double)pit / ms : 0.0;
         if (std::getenv("MD_AUTOTUNE_LOG"))
             std::fprintf(stderr, "md autotune: variant %d block %d ctas/SM %d: %.3f ms, %.3g point-iterations/s\n",
@@ -394,6 +402,10 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     const int Pn = poles->n_poles;
     const long long n_sys = nn * Pn;
     if (n_sys > (1LL << 31) - 1) return set_error(MD_ERR_INVALID, "too many systems");
+    const bool ms = opts.method == 1;
+    if (ms && ckpt) return set_error(MD_ERR_INVALID, "method 1 (shifted COCG) keeps no checkpoint");
+    if (ms && Pn > 64) return set_error(MD_ERR_INVALID, "method 1 (shifted COCG) handles at most 64 poles");
+    if (ms && opts.kernel == 2) return set_error(MD_ERR_INVALID, "method 1 runs on the generic kernel");
 
     md_plan* pl = new md_plan();
     pl->H = &H;
@@ -405,6 +417,7 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     pl->rho_out = rho_out;
     pl->e_out = e_out;
     pl->own_scratch = !borrow_scratch;
+    pl->multishift = ms;
     std::memset(&pl->P, 0, sizeof(pl->P));
     auto fail = [&](md_status s) {
         plan_free(pl);
@@ -428,16 +441,26 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     PTRY(cudaGetDevice(&dev));
     PTRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
 
-    // cost-sorted work list: big regions first, then poles nearest the real axis
-    std::vector<SysDesc> sys(n_sys);
-    for (long long j = 0; j < nn; ++j)
-        for (int p = 0; p < Pn; ++p) sys[j * Pn + p] = SysDesc{(int)j, p};
+    // cost-sorted work list: big regions first, then poles nearest the real axis;
+    // with shifted COCG one item per node, seeded by the pole nearest the axis
+    std::vector<SysDesc> sys;
+    if (ms) {
+        int seed = 0;
+        for (int p = 1; p < Pn; ++p)
+            if (poles->z[2 * p + 1] < poles->z[2 * seed + 1]) seed = p;
+        for (long long j = 0; j < nn; ++j) sys.push_back(SysDesc{(int)j, seed});
+    } else {
+        sys.resize(n_sys);
+        for (long long j = 0; j < nn; ++j)
+            for (int p = 0; p < Pn; ++p) sys[j * Pn + p] = SysDesc{(int)j, p};
+    }
     std::stable_sort(sys.begin(), sys.end(), [&](const SysDesc& a, const SysDesc& b) {
         const double ca = (double)R.points[a.node] / std::sqrt(poles->z[2 * a.pole + 1]);
         const double cb = (double)R.points[b.node] / std::sqrt(poles->z[2 * b.pole + 1]);
         return ca > cb;
     });
-    PTRY(cudaMalloc(&pl->d_sys, n_sys * sizeof(SysDesc)));
+    const long long n_work = (long long)sys.size();
+    PTRY(cudaMalloc(&pl->d_sys, n_work * sizeof(SysDesc)));
     PTRY(cudaMalloc(&pl->d_nodes, nn * sizeof(NodeDesc)));
     PTRY(cudaMalloc(&pl->d_status, n_sys * sizeof(int)));
     PTRY(cudaMalloc(&pl->d_iters, n_sys * sizeof(int)));
@@ -447,7 +470,7 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     PTRY(cudaMalloc(&pl->d_z, Pn * sizeof(double2)));
     PTRY(cudaMalloc(&pl->d_w, Pn * sizeof(double2)));
     PTRY(cudaMalloc(&pl->d_counter, sizeof(unsigned int)));
-    PTRY(cudaMemcpy(pl->d_sys, sys.data(), n_sys * sizeof(SysDesc), cudaMemcpyHostToDevice));
+    PTRY(cudaMemcpy(pl->d_sys, sys.data(), n_work * sizeof(SysDesc), cudaMemcpyHostToDevice));
     PTRY(cudaMemcpy(pl->d_nodes, R.desc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice));
     PTRY(cudaMemcpy(pl->d_z, poles->z, Pn * sizeof(double2), cudaMemcpyHostToDevice));
     PTRY(cudaMemcpy(pl->d_w, poles->w, Pn * sizeof(double2), cudaMemcpyHostToDevice));
@@ -489,7 +512,8 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     P.pl_val64 = H.pl_val64;
     P.e_s = H.e_s;
     P.e_p = H.e_p;
-    P.n_sys = (int)n_sys;
+    P.n_sys = (int)n_work;
+    P.multishift = ms ? 1 : 0;
     P.P = Pn;
     P.sys = pl->d_sys;
     P.nodes = pl->d_nodes;
@@ -511,12 +535,12 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     P.n_rel = pl->d_nrel;
 
     const int max_plane = R.max_dim[0] * R.max_dim[1];
-    const bool zm_ok = zm_supported(opts.precision, H.q) && !R.any_ring;
+    const bool zm_ok = zm_supported(opts.precision, H.q) && !R.any_ring && !ms;
     P.zm_m0 = R.max_dim[0];
     P.zm_m1 = R.max_dim[1];
     if (zm_ok) pl->smem = zm_smem_bytes(H.q, R.max_dim[0], R.max_dim[1]);
     // scratch sized for the widest candidate (2 CTAs per SM)
-    const int max_ctas = (int)std::min<long long>((long long)n_sm * 2, n_sys);
+    const int max_ctas = (int)std::min<long long>((long long)n_sm * 2, n_work);
     const size_t need = P.slot_bytes * (size_t)max_ctas;
     if (borrow_scratch) {
         if (need > H.scratch_bytes) {
@@ -551,7 +575,7 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     shape.per_sm = std::min(shape.per_sm, 2);
     pl->variant = shape.variant;
     pl->block = shape.block;
-    pl->grid = (int)std::min<long long>((long long)n_sm * shape.per_sm, n_sys);
+    pl->grid = (int)std::min<long long>((long long)n_sm * shape.per_sm, n_work);
 
     // capture [reset counter, solver, accumulation] once; launches replay it
     PTRY(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
@@ -613,10 +637,16 @@ md_status plan_stats(md_plan* pl, cudaStream_t stream, md_stats* stats) {
         sst.iters_min = std::min(sst.iters_min, h_iters[k]);
         sst.iters_max = std::max(sst.iters_max, h_iters[k]);
         sst.total_iters += h_iters[k];
-        sst.total_point_iters += (long long)h_iters[k] * pl->points[k / pl->Pn];
+        if (!pl->multishift) sst.total_point_iters += (long long)h_iters[k] * pl->points[k / pl->Pn];
         sst.reliable_updates += h_nrel[k];
         sst.max_resid = std::max(sst.max_resid, h_resid[k]);
     }
+    if (pl->multishift)   // one matvec sequence per node: as long as its slowest pole
+        for (long long j = 0; j < pl->nn; ++j) {
+            int mx = 0;
+            for (int p = 0; p < pl->Pn; ++p) mx = std::max(mx, h_iters[j * pl->Pn + p]);
+            sst.total_point_iters += (long long)mx * pl->points[j];
+        }
     sst.iters_mean = (double)sst.total_iters / (double)n_sys;
     sst.kernel_ms = ms;
     if (stats) *stats = sst;

@@ -49,6 +49,7 @@ constexpr int kLocal = kMaxLocalProjAtoms;
 constexpr int kMapMax = 4096;   // direct global->local atom map when n_atoms <= this
 constexpr int kChunk = 8;       // points per FP32 partial sum before it joins the FP64 sum
 constexpr int kStop = 1, kRefresh = 2, kStopTimeout = 3;
+constexpr int kMaxShifts = 64;
 
 // Per-thread partial sum: compensated (Kahan) in float, plain in double.
 // The float partial is rounded to double once, where the block reduction
@@ -68,6 +69,14 @@ struct KSum<float> {
     __device__ __forceinline__ float hi() const { return s; }
     __device__ __forceinline__ float lo() const { return -c; }
 };
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
 struct MixedModeT {
     using real = float;
     using cplx = float2;
@@ -146,6 +155,13 @@ struct Shared {
     double2 c[kLocal][4];   // E_l dV C_l sum_i f_l(i) v(i), double
     double2 pnl[32];        // per warp: sum over its atoms of E_l dV c_l^2 (v^T V_nl v)
     float cacc[kLocal][8];  // z-march: raw projections sum_i f_l(i) v(i), accumulated per plane
+    // shifted COCG (one Krylov sequence per node for all poles), per pole k:
+    double2 sh_pi_prev[kMaxShifts], sh_pi[kMaxShifts];   // pi_{n-1}, pi_n
+    double2 sh_x[kMaxShifts], sh_p[kMaxShifts];          // x_k(j), p_k(j)
+    int sh_conv[kMaxShifts];                             // iteration at which pole k met tol, or 0
+    double2 rj;                                          // seed residual at the node
+    double alpha_prev[2], beta_prev[2];
+    int all_conv;
     uint64_t bar[4];        // z-march: staging-slot mbarriers
     float2 cf[kLocal][4];   // the same rounded to float
     short map[kMapMax];     // global atom id -> local slot, -1 if absent
@@ -452,8 +468,33 @@ struct PVal<double> {
     __device__ static double2 c(const Shared& S, int k, int l) { return S.c[k][l]; }
 };
 
-// y = (H_R - z) v at region point i (Q = stencil half-width), arithmetic in R.
-template <class R, class C, int Q, class CIn>
+// Nonlocal part of (H_R v)(i) from the coefficients in S.cf (mixed path):
+// the point's projector list (global CSR) with its four stored values.
+__device__ __forceinline__ float2 nl_apply(const SolveParams& P, const Geo& G, const Shared& S, int i) {
+    const int c = (int)fdiv((uint32_t)i, G.div_plane);
+    const int rem = i - c * G.plane;
+    const int b = (int)fdiv((uint32_t)rem, G.div_row);
+    const int a = rem - b * G.m[0];
+    const int gx = wrap_once(G.lo[0] + a, P.n[0]);
+    const int gy = wrap_once(G.lo[1] + b, P.n[1]);
+    const int gz = wrap_once(G.lo[2] + c, P.n[2]);
+    const long long gi = gx + (long long)P.n[0] * (gy + (long long)P.n[1] * gz);
+    float yx = 0.f, yy = 0.f;
+    const int e0 = __ldg(P.pl_ptr + gi), e1 = __ldg(P.pl_ptr + gi + 1);
+    for (int e = e0; e < e1; ++e) {
+        const int k = local_slot(P, S, __ldg(P.pl_atom + e));
+        if (k < 0) continue;
+        const float4 f = __ldg(P.pl_val32 + e);
+        const float2 c0 = S.cf[k][0], c1 = S.cf[k][1], c2 = S.cf[k][2], c3 = S.cf[k][3];
+        yx += f.x * c0.x + f.y * c1.x + f.z * c2.x + f.w * c3.x;
+        yy += f.x * c0.y + f.y * c1.y + f.z * c2.y + f.w * c3.y;
+    }
+    return make_float2(yx, yy);
+}
+
+// y = (H_R - z) v at region point i (Q = stencil half-width), arithmetic in R;
+// kNl = false leaves out the nonlocal term (added elsewhere).
+template <class R, class C, int Q, class CIn, bool kNl = true>
 __device__ __forceinline__ C matvec_point(const SolveParams& P, const Geo& G, const Shared& S,
                                           const CIn* __restrict__ v, int i, R zr, R zi, R diag) {
     const int c = (int)fdiv((uint32_t)i, G.div_plane);
@@ -522,7 +563,7 @@ __device__ __forceinline__ C matvec_point(const SolveParams& P, const Geo& G, co
             }
         }
     }
-    if (P.nonlocal) {
+    if (kNl && P.nonlocal) {
         const int e0 = __ldg(P.pl_ptr + gi), e1 = __ldg(P.pl_ptr + gi + 1);
         for (int e = e0; e < e1; ++e) {
             const int k = local_slot(P, S, __ldg(P.pl_atom + e));
@@ -567,6 +608,7 @@ __device__ __noinline__ void refresh_residual(const SolveParams& P, const Geo& G
         const double tim = -y.y;
         const C rr = cmake<C>((R)tre, (R)tim);
         r[i] = rr;
+        if (P.multishift && i == G.src) S.rj = make_double2((double)rr.x, (double)rr.y);
         q_re.add(rr.x * rr.x - rr.y * rr.y);
         q_im.add(2 * rr.x * rr.y);
         nrm += tre * tre + tim * tim;
@@ -576,6 +618,61 @@ __device__ __noinline__ void refresh_residual(const SolveParams& P, const Geo& G
     t3[2] = nrm;
     block_reduce<3>(S, t3);
 }
+
+// Shifted COCG: one step of the P pole recurrences (warp 0; lane k updates
+// poles k, k+32, ...).  With sigma_k = z_seed - z_k the shifted residuals are
+// r / pi_k (Jegerlehner 1996; Takayama et al. 2006 for COCG):
+//   pi_{n+1} = (1 + a_n sigma) pi_n + (a_n b_{n-1}/a_{n-1}) (pi_n - pi_{n-1})
+//   a_k = a_n pi_n/pi_{n+1},  b_k = (pi_n/pi_{n+1})^2 b_n
+//   x_k(j) += a_k p_k(j),  p_k(j) = r(j)/pi_{n+1} + b_k p_k(j)
+// Only the node's entries are tracked: the density needs x_k(j) alone.  A
+// pole counts as converged once ||r|| / |pi_k| <= tol and is then frozen.
+__device__ __noinline__ void shifted_update(const SolveParams& P, Shared& S) {
+
+                    const double2 an = make_double2(S.alpha[0], S.alpha[1]);
+                    const double2 bn = (S.action == kStop) ? make_double2(0.0, 0.0) : make_double2(S.beta[0], S.beta[1]);
+                    const double2 ap = make_double2(S.alpha_prev[0], S.alpha_prev[1]);
+                    const double2 bp = make_double2(S.beta_prev[0], S.beta_prev[1]);
+                    const double2 c3 = zdiv(zmul(an, bp), ap);
+                    const double2 zs = P.z[P.sys[S.sys].pole];
+                    const double2 rj = S.rj;
+                    bool all = true;
+                    for (int k = threadIdx.x; k < P.P; k += 32) {
+                        if (!S.sh_conv[k]) {
+                            const double2 zk = P.z[k];
+                            const double2 sg = make_double2(zs.x - zk.x, zs.y - zk.y);
+                            const double2 pc = S.sh_pi[k], pp = S.sh_pi_prev[k];
+                            const double2 t1 = zmul(make_double2(1.0 + (an.x * sg.x - an.y * sg.y), an.x * sg.y + an.y * sg.x), pc);
+                            const double2 t2 = zmul(c3, make_double2(pc.x - pp.x, pc.y - pp.y));
+                            const double2 pn = make_double2(t1.x + t2.x, t1.y + t2.y);
+                            const double2 ratio = zdiv(pc, pn);
+                            const double2 ak = zmul(an, ratio);
+                            const double2 bk = zmul(zmul(ratio, ratio), bn);
+                            const double2 xk = S.sh_x[k], pk = S.sh_p[k];
+                            const double2 axp = zmul(ak, pk);
+                            S.sh_x[k] = make_double2(xk.x + axp.x, xk.y + axp.y);
+                            const double2 rq = zdiv(rj, pn), bpk = zmul(bk, pk);
+                            S.sh_p[k] = make_double2(rq.x + bpk.x, rq.y + bpk.y);
+                            S.sh_pi_prev[k] = pc;
+                            S.sh_pi[k] = pn;
+                            const double apn = sqrt(pn.x * pn.x + pn.y * pn.y);
+                            if (S.rn <= P.tol * apn) S.sh_conv[k] = S.it;
+                        }
+                        all = all && (S.sh_conv[k] != 0);
+                    }
+                    all = __all_sync(0xffffffffu, all);
+                    if (threadIdx.x == 0) {
+                        S.alpha_prev[0] = an.x;
+                        S.alpha_prev[1] = an.y;
+                        S.beta_prev[0] = bn.x;
+                        S.beta_prev[1] = bn.y;
+                        if (all && S.action != kStop) {
+                            S.st = 0;
+                            S.action = kStop;
+                        }
+                        if (S.action == kStop && S.st != 0 && all) S.st = 0;
+                    }
+                }
 
 template <class Mode, int Q>
 __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolveParams P) {
@@ -627,6 +724,14 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
         if (P.ckpt) x = P.ckpt + P.ckpt_sys_off[out_idx];
 
         if (P.nonlocal) collect_local_atoms(P, G, S);
+        if (P.multishift)
+            for (int k = threadIdx.x; k < P.P; k += blockDim.x) {
+                S.sh_pi_prev[k] = make_double2(1.0, 0.0);
+                S.sh_pi[k] = make_double2(1.0, 0.0);
+                S.sh_x[k] = make_double2(0.0, 0.0);
+                S.sh_p[k] = make_double2(1.0, 0.0);   // p_0 = b, b(j) = 1
+                S.sh_conv[k] = 0;
+            }
 
         for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
             r[i] = cmake<C>((R)(i == G.src ? 1 : 0), (R)0);
@@ -650,6 +755,11 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
             S.n_rel = 0;
             S.restart = 0;
             S.st = 2;   // not converged
+            S.alpha_prev[0] = 1.0;
+            S.alpha_prev[1] = 0.0;
+            S.beta_prev[0] = 0.0;
+            S.beta_prev[1] = 0.0;
+            S.all_conv = 0;
         }
         __syncthreads();
 
@@ -741,6 +851,8 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                         rv.w -= ar * qv.w + ai * qv.z;
                         d4[k] = d;
                         r4[k] = rv;
+                        if (P.multishift && (G.src >> 1) == k)
+                            S.rj = (G.src & 1) ? make_double2(rv.z, rv.w) : make_double2(rv.x, rv.y);
                         s_re.add(rv.x * rv.x - rv.y * rv.y + (rv.z * rv.z - rv.w * rv.w));
                         s_im.add(2.f * (rv.x * rv.y + rv.z * rv.w));
                         s_n.add(rv.x * rv.x + rv.y * rv.y + (rv.z * rv.z + rv.w * rv.w));
@@ -755,6 +867,7 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                         ri.y -= ar * api.y + ai * api.x;
                         dx[i] = d;
                         r[i] = ri;
+                        if (P.multishift && i == G.src) S.rj = make_double2(ri.x, ri.y);
                         s_re.add(ri.x * ri.x - ri.y * ri.y);
                         s_im.add(2.f * ri.x * ri.y);
                         s_n.add(ri.x * ri.x + ri.y * ri.y);
@@ -770,6 +883,7 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                         ri.x -= ar * api.x - ai * api.y;
                         ri.y -= ar * api.y + ai * api.x;
                         r[i] = ri;
+                        if (P.multishift && i == G.src) S.rj = make_double2((double)ri.x, (double)ri.y);
                         s_re.add(ri.x * ri.x - ri.y * ri.y);
                         s_im.add(2 * ri.x * ri.y);
                         s_n.add(ri.x * ri.x + ri.y * ri.y);
@@ -811,11 +925,15 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                 S.rn = rn;
                 S.action = 0;
                 const double rr_abs = sqrt(red3[0] * red3[0] + red3[1] * red3[1]);
-                if (rn <= P.tol) {
+                if (rn <= P.tol && !P.multishift) {
                     S.st = 0;
                     S.action = kStop;
                 } else if (!(rr_abs > 1e-300) || rr_abs < 1e-14 * rn * rn) {
-                    S.st = 3;
+                    if (rn <= P.tol) {
+                        S.st = 0;   // converged exactly: no further direction needed
+                    } else {
+                        S.st = 3;
+                    }
                     S.action = kStop;
                 } else {
                     const double rd = S.rho[0] * S.rho[0] + S.rho[1] * S.rho[1];
@@ -827,6 +945,10 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                 S.restart = 0;
             }
             __syncthreads();
+            if (P.multishift) {   // shifted systems share the seed's Krylov space
+                if (threadIdx.x < 32) shifted_update(P, S);
+                __syncthreads();
+            }
             if (S.action == kStop) break;
         }
         const bool timed_out = (S.action == kStopTimeout);
@@ -842,7 +964,17 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (P.multishift) {
+            for (int k = threadIdx.x; k < P.P; k += blockDim.x) {
+                const long long o = (long long)sd.node * P.P + k;
+                const double2 pk = S.sh_pi[k];
+                P.x_src[o] = S.sh_x[k];
+                P.status[o] = timed_out ? 4 : (S.flag ? 1 : (S.sh_conv[k] ? 0 : (status == 3 ? 3 : 2)));
+                P.iters[o] = S.sh_conv[k] ? S.sh_conv[k] : S.it;
+                P.resid[o] = S.rn / sqrt(pk.x * pk.x + pk.y * pk.y);
+                P.n_rel[o] = (k == sd.pole) ? S.n_rel : 0;
+            }
+        } else if (threadIdx.x == 0) {
             P.x_src[out_idx] = x[G.src];
             P.status[out_idx] = timed_out ? 4 : (S.flag ? 1 : status);
             P.iters[out_idx] = S.it;

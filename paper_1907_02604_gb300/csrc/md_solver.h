@@ -66,6 +66,7 @@ struct SolveParams {
     size_t slot_bytes;
     int n_max;                      // vector length per slot (rounded up)
     int zm_m0, zm_m1;               // z-march kernel: largest region extents in x, y
+    int multishift;                 // 1: one shifted-COCG sequence per node (work items are nodes)
     double2* ckpt;                  // NULL or checkpoint base
     const long long* ckpt_sys_off;  // point offset of system (node*P + pole) in ckpt
     unsigned int* work_counter;
