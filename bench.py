@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--maxit", type=int, default=0, help="iteration cap (profiling runs)")
+    ap.add_argument("--method", default="cocg", choices=["cocg", "shifted"])
+    ap.add_argument("--no-shifted", action="store_true", help="skip the shifted-COCG side measurement")
     return ap.parse_args()
 
 
@@ -212,7 +214,7 @@ def main():
     bs = min(args.nodes_per_step, n_nodes)
     n_batches = max(1, n_nodes // bs)
     opts = SolverOptions(tol=w.tol, maxit=args.maxit or w.maxit, precision=prec, block=args.block,
-                         ctas_per_sm=args.ctas_per_sm)
+                         ctas_per_sm=args.ctas_per_sm, method=args.method)
     stream = torch.cuda.current_stream()
 
     def batch(i):
@@ -270,6 +272,33 @@ def main():
     achieved = point_iters * B / (kernel_ms / 1e3) / 1e9
     peak, peak_kind = read_peaks()
     shape = plans[0].launch_shape()
+
+    # ---- side measurement: shifted COCG (one Krylov sequence per node) -----
+    shifted = None
+    if args.method == "cocg" and not args.no_shifted:
+        from dataclasses import replace as _replace
+        sopts = _replace(opts, method="shifted", block=0, ctas_per_sm=0)
+        splans = [Plan(ham, z, wt, *batch(i), sopts, energy=True, stream=stream) for i in range(n_plans)]
+        for i in range(args.warmup):
+            splans[i % n_plans].launch(stream)
+            splans[i % n_plans].stats(stream, strict=False)
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for i in range(args.steps):
+            splans[(args.warmup + i) % n_plans].launch(stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        sms = s0.elapsed_time(s1)
+        sst = [splans[(args.warmup + i) % n_plans].stats(stream, strict=False) for i in range(args.steps)]
+        shifted = {"value": sum(x["n_systems"] for x in sst) * world / (sms / 1e3), "unit": "solves/s",
+                   "ms_per_step": sms / args.steps,
+                   "converged": f"{sum(x['n_converged'] for x in sst)}/{sum(x['n_systems'] for x in sst)}",
+                   "point_iters_per_s": sum(x["total_point_iters"] for x in sst) * world / (sms / 1e3),
+                   "note": "method 1: per node one Krylov sequence serves all poles (density only)"}
+        for sp in splans:
+            sp.close()
 
     # ---- end to end through the C ABI from host buffers -------------------
     e2e = None
@@ -341,6 +370,7 @@ def main():
                      "bytes_per_point_iter": B, "peak_kind": peak_kind},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "shifted_cocg": shifted,
         "gpu_launches": 2 * args.steps,
         "launch_shape": {"threads_per_cta": shape[0], "ctas": shape[1]},
         "clocks": clocks,

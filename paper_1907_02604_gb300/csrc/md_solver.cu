@@ -46,7 +46,7 @@ namespace md {
 namespace {
 
 constexpr int kLocal = kMaxLocalProjAtoms;
-constexpr int kMapMax = 4096;   // direct global->local atom map when n_atoms <= this
+constexpr int kMapMax = 2048;   // direct global->local atom map when n_atoms <= this
 constexpr int kChunk = 8;       // points per FP32 partial sum before it joins the FP64 sum
 constexpr int kStop = 1, kRefresh = 2, kStopTimeout = 3;
 constexpr int kMaxShifts = 64;
@@ -154,7 +154,6 @@ struct Shared {
     short la_off[kLocal][3];
     double2 c[kLocal][4];   // E_l dV C_l sum_i f_l(i) v(i), double
     double2 pnl[32];        // per warp: sum over its atoms of E_l dV c_l^2 (v^T V_nl v)
-    float cacc[kLocal][8];  // z-march: raw projections sum_i f_l(i) v(i), accumulated per plane
     // shifted COCG (one Krylov sequence per node for all poles), per pole k:
     double2 sh_pi_prev[kMaxShifts], sh_pi[kMaxShifts];   // pi_{n-1}, pi_n
     double2 sh_x[kMaxShifts], sh_p[kMaxShifts];          // x_k(j), p_k(j)
@@ -1017,11 +1016,12 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 // Dynamic shared memory of the z-march kernel for launch-wide maximal
 // region extents M0 x M1 (the same arithmetic on host and device).
 struct ZmLayout {
-    size_t plane_off, nl_off, stage_off, stage_bytes, total;
+    size_t cacc_off, plane_off, nl_off, stage_off, stage_bytes, total;
     __host__ __device__ ZmLayout(int q, int M0, int M1) {
         const size_t pb = (size_t)(M0 + 2 * q) * (size_t)(M1 + 2 * q);   // bordered plane
         const size_t pl = (size_t)M0 * (size_t)M1;
-        plane_off = 0;
+        cacc_off = 0;                                                       // float [kLocal][8]
+        plane_off = (size_t)kLocal * 8 * sizeof(float);
         nl_off = plane_off + 2 * pb * sizeof(float2);
         stage_bytes = (pl * sizeof(float2) + 16 + 15) / 16 * 16;          // one staged plane
         stage_off = (nl_off + 2 * pl * sizeof(float2) + 127) / 128 * 128;
@@ -1055,10 +1055,11 @@ __device__ __forceinline__ void zm_issue(const SolveParams& P, const Geo& G, uns
 }
 
 // Projections of the published plane c (bordered buffer, row pitch `pitch`,
-// border width q) onto the local projectors, added into S.cacc: warp per
+// border width q) onto the local projectors, added into cacc[k][8]: warp per
 // local atom, lane per row of the disk where its sphere cuts the plane.
 __device__ __noinline__ void zm_nl_dot_plane(const SolveParams& P, const Geo& G, Shared& S,
-                                             const float2* __restrict__ buf, int pitch, int Q, int c) {
+                                             const float2* __restrict__ buf, int pitch, int Q, int c,
+                                             float* __restrict__ cacc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int m0 = G.m[0], m1 = G.m[1];
             for (int kk = warp; kk < S.n_local; kk += nw) {
@@ -1102,7 +1103,7 @@ __device__ __noinline__ void zm_nl_dot_plane(const SolveParams& P, const Geo& G,
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const float v = warp_sum(acc8[t]);
-                    if (lane == 0) atomicAdd(&S.cacc[kk][t], v);
+                    if (lane == 0) atomicAdd(&cacc[kk * 8 + t], v);
                 }
             }
         }
@@ -1118,7 +1119,7 @@ __device__ __noinline__ void zm_nl_dot_plane(const SolveParams& P, const Geo& G,
 // also accumulate the nonlocal coefficients c_al over the disk where each
 // local atom's projector sphere cuts that plane (separable Gaussian: per
 // row A = sum g_x v, B = sum d_x g_x v).  Outputs: p (new), Ap_loc =
-// (-1/2 L + V - z) p, S.cacc (raw projections), the thread's p^T Ap_loc.
+// (-1/2 L + V - z) p, cacc (raw projections), the thread's p^T Ap_loc.
 template <int Q, int K>
 __device__ __forceinline__ void zm_stencil_pass(const SolveParams& P, const Geo& G, Shared& S,
                                                 unsigned char* dsm, const ZmLayout& L, uint32_t& ph,
@@ -1133,6 +1134,7 @@ __device__ __forceinline__ void zm_stencil_pass(const SolveParams& P, const Geo&
     const long long nxy = (long long)P.n[0] * P.n[1];
     const float* cf = coef_of<float>(S);
     float2* pbuf = reinterpret_cast<float2*>(dsm + L.plane_off);
+    float* cacc = reinterpret_cast<float*>(dsm + L.cacc_off);
     unsigned char* stage = dsm + L.stage_off;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
     // staging offset (elements) of the plane start inside a 16-byte aligned copy
@@ -1142,7 +1144,7 @@ __device__ __forceinline__ void zm_stencil_pass(const SolveParams& P, const Geo&
     bool ok[K];
     float2 win[K][2 * Q + 1];
     if (P.nonlocal)
-        for (int t = threadIdx.x; t < S.n_local * 8; t += T) (&S.cacc[0][0])[t] = 0.f;
+        for (int t = threadIdx.x; t < S.n_local * 8; t += T) cacc[t] = 0.f;
     if (threadIdx.x == 0)
         for (int cn = Q + 1; cn < m2 && cn <= Q + kStages - 1; ++cn) zm_issue(P, G, stage, L.stage_bytes, S.bar, r, p, cn);
 #pragma unroll
@@ -1221,7 +1223,7 @@ __device__ __forceinline__ void zm_stencil_pass(const SolveParams& P, const Geo&
                 acc_im.add(ctr.x * yy + ctr.y * yx);
             }
         }
-        if (P.nonlocal) zm_nl_dot_plane(P, G, S, buf, pitch, Q, c);
+        if (P.nonlocal) zm_nl_dot_plane(P, G, S, buf, pitch, Q, c, cacc);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
 #pragma unroll
@@ -1391,9 +1393,10 @@ __global__ void __launch_bounds__(ZmThreads<K>::value) k_cocg_zm(const __grid_co
             float hi[2] = {acc_re.hi(), acc_im.hi()}, lo[2] = {acc_re.lo(), acc_im.lo()};
             if (P.nonlocal) {
                 // coefficients E_l dV C_l s_l and the bilinear energy E_l dV (C_l s_l)^2
+                const float* cacc = reinterpret_cast<const float*>(dsm + L.cacc_off);
                 for (int t = threadIdx.x; t < S.n_local * 4; t += blockDim.x) {
                     const int kk = t >> 2, l = t & 3;
-                    const double sr = S.cacc[kk][2 * l], si = S.cacc[kk][2 * l + 1];
+                    const double sr = cacc[kk * 8 + 2 * l], si = cacc[kk * 8 + 2 * l + 1];
                     const double Cl = __ldg(P.proj_C + 4LL * S.la_id[kk] + l);
                     const double E = (l == 0 ? P.e_s : P.e_p) * P.dV * Cl;
                     S.c[kk][l] = make_double2(E * sr, E * si);
@@ -1550,11 +1553,8 @@ cudaError_t launch_q(const SolveParams& P, int grid, int block, cudaStream_t str
 
 template <int Q, int K>
 cudaError_t launch_zm_k(const SolveParams& P, int grid, int block, size_t smem, cudaStream_t stream) {
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_cocg_zm<Q, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
-        configured = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(k_cocg_zm<Q, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     k_cocg_zm<Q, K><<<grid, block, smem, stream>>>(P);
     return cudaGetLastError();
 }
@@ -1586,7 +1586,10 @@ bool zm_supported(int precision, int q) { return precision == MD_PREC_MIXED && (
 
 template <int Q, int K>
 int zm_occ_k(int block, size_t smem) {
-    cudaFuncSetAttribute(k_cocg_zm<Q, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
+    if (cudaFuncSetAttribute(k_cocg_zm<Q, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cocg_zm<Q, K>, block, smem) != cudaSuccess) {
         cudaGetLastError();
