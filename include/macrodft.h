@@ -212,6 +212,26 @@ md_status md_energy(const md_hamiltonian* ham, const md_poles* poles,
                     const md_nodes* nodes, const md_solver_opts* opts,
                     double* e_out, double* e_band, md_stats* stats, void* stream);
 
+/* Density, band energy and the adjoint in one pass, without a checkpoint,
+ * for losses whose node sensitivities a_j = dL/drho_j and b_j = dL/de_j are
+ * known before the solve (for example the band energy, L = E_band: a = 0,
+ * b = 1; the Hellmann-Feynman forces of Section 2.1 follow).  Each system,
+ * once converged, adds its share
+ *     -Im((2 a_j/dV + 2 b_j z_p) w_p x_jp(k)^2)
+ * to dL_dV_out (device, N doubles, zeroed first) while its solution is still
+ * in the solver's scratch, so memory stays one region per resident CTA
+ * instead of the 16 P sum_j |R(j)| bytes of md_workspace_create.
+ *   dL_drho, dL_de: device, n_nodes each, or NULL (= 0).
+ *   rho_out (device, n_nodes), e_out (device or NULL), forces_out (device,
+ *   3 n_atoms, or NULL; needs atoms and no nonlocal term).
+ * Per-pole COCG only (method 0).  Synchronises `stream`.  Status as for
+ * md_density; dL_dV accumulates with FP64 atomics. */
+md_status md_density_fused_adjoint(const md_hamiltonian* ham, const md_poles* poles,
+                                   const md_nodes* nodes, const md_solver_opts* opts,
+                                   const double* dL_drho, const double* dL_de, double* rho_out,
+                                   double* e_out, double* dL_dV_out, double* forces_out,
+                                   md_stats* stats, void* stream);
+
 /* ---- Plans: a prepared batched solve replayed as a CUDA graph ----------
  * md_plan_create validates the inputs once, uploads the cost-sorted
  * (node, pole) work list and region descriptors, allocates the plan's own

@@ -300,6 +300,29 @@ def energy(ham: Hamiltonian, z, w, nodes, halfwidth, opts: SolverOptions = None,
     return e, eb.value, st.as_dict()
 
 
+def density_fused_adjoint(ham: Hamiltonian, z, w, nodes, halfwidth, dL_drho: torch.Tensor = None,
+                          dL_de: torch.Tensor = None, opts: SolverOptions = None, forces=False,
+                          stream=None):
+    """rho, e, dL/dV (and forces) in one pass without a checkpoint, for node
+    sensitivities known before the solve (e.g. the band energy: dL_de = 1)."""
+    opts = opts or SolverOptions()
+    pa, na = _PoleArgs(z, w), _NodeArgs(nodes, halfwidth)
+    a = None if dL_drho is None else _cuda_f64(dL_drho, na.n, "dL_drho")
+    b = None if dL_de is None else _cuda_f64(dL_de, na.n, "dL_de")
+    rho = torch.empty(na.n, dtype=torch.float64, device="cuda")
+    e = torch.empty(na.n, dtype=torch.float64, device="cuda")
+    g = torch.empty(ham.N, dtype=torch.float64, device="cuda")
+    F = torch.empty(3 * ham.n_atoms, dtype=torch.float64, device="cuda") if forces else None
+    st = _lib.md_stats()
+    copts = opts.to_c()
+    vp = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    check(load().md_density_fused_adjoint(ham.handle, ctypes.byref(pa.c), ctypes.byref(na.c),
+                                          ctypes.byref(copts), vp(a), vp(b), vp(rho), vp(e), vp(g), vp(F),
+                                          ctypes.byref(st), _stream_handle(stream)),
+          "md_density_fused_adjoint")
+    return rho, e, g, (F.view(-1, 3) if F is not None else None), st.as_dict()
+
+
 def density_adjoint(ham: Hamiltonian, z, w, nodes, halfwidth, dL_drho: torch.Tensor,
                     dL_de: torch.Tensor = None, opts: SolverOptions = None,
                     checkpoint: Workspace = None, forces=False, stream=None):

@@ -342,7 +342,8 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
         T.sys = d_sample;
         T.n_sys = (int)ns;
         T.maxit = std::min(pl->P.maxit, 48);
-        T.ckpt = nullptr;   // trials never touch the checkpoint
+        T.ckpt = nullptr;         // trials never touch the checkpoint
+        T.fused_dLdV = nullptr;   // nor the gradient
         const int grid = (int)std::min<long long>((long long)n_sm * c.per_sm, ns);
         if (pl->P.slot_bytes * (size_t)grid > scratch_bytes) continue;
         cudaMemset(T.work_counter, 0, sizeof(unsigned int));
@@ -382,9 +383,16 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
     return MD_OK;
 }
 
+struct FusedArgs {
+    double* dLdV;
+    const double* a;
+    const double* b;
+};
+
 md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,
                       const md_solver_opts* opts_in, double* rho_out, double* e_out, md_workspace* ckpt,
-                      bool borrow_scratch, cudaStream_t stream, md_plan** out) {
+                      bool borrow_scratch, cudaStream_t stream, md_plan** out,
+                      const FusedArgs* fused = nullptr) {
     *out = nullptr;
     md_status st = check_device();
     if (st != MD_OK) return st;
@@ -406,6 +414,7 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     if (ms && ckpt) return set_error(MD_ERR_INVALID, "method 1 (shifted COCG) keeps no checkpoint");
     if (ms && Pn > 64) return set_error(MD_ERR_INVALID, "method 1 (shifted COCG) handles at most 64 poles");
     if (ms && opts.kernel == 2) return set_error(MD_ERR_INVALID, "method 1 runs on the generic kernel");
+    if (fused && ms) return set_error(MD_ERR_INVALID, "the fused adjoint needs method 0");
 
     md_plan* pl = new md_plan();
     pl->H = &H;
@@ -514,6 +523,12 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     P.e_p = H.e_p;
     P.n_sys = (int)n_work;
     P.multishift = ms ? 1 : 0;
+    P.w = pl->d_w;
+    if (fused) {
+        P.fused_dLdV = fused->dLdV;
+        P.fused_a = fused->a;
+        P.fused_b = fused->b;
+    }
     P.P = Pn;
     P.sys = pl->d_sys;
     P.nodes = pl->d_nodes;
@@ -535,7 +550,7 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     P.n_rel = pl->d_nrel;
 
     const int max_plane = R.max_dim[0] * R.max_dim[1];
-    const bool zm_ok = zm_supported(opts.precision, H.q) && !R.any_ring && !ms;
+    const bool zm_ok = zm_supported(opts.precision, H.q) && !R.any_ring && !ms && !fused;
     P.zm_m0 = R.max_dim[0];
     P.zm_m1 = R.max_dim[1];
     if (zm_ok) pl->smem = zm_smem_bytes(H.q, R.max_dim[0], R.max_dim[1]);
@@ -1230,6 +1245,58 @@ done:
         md_workspace_destroy(own);
     }
     return st;
+}
+
+md_status md_density_fused_adjoint(const md_hamiltonian* ham, const md_poles* poles,
+                                   const md_nodes* nodes, const md_solver_opts* opts,
+                                   const double* dL_drho, const double* dL_de, double* rho_out,
+                                   double* e_out, double* dL_dV_out, double* forces_out, md_stats* stats,
+                                   void* stream) {
+    clear_error();
+    md_status st = check_device();
+    if (st != MD_OK) return st;
+    if (!ham || !dL_dV_out) return set_error(MD_ERR_INVALID, "ham and dL_dV_out are required");
+    const Ham& H = ham->h;
+    if (forces_out && H.nonlocal && H.n_atoms > 0)
+        return set_error(MD_ERR_INVALID, "forces need a Hamiltonian without the nonlocal term");
+    if (forces_out && H.n_atoms == 0) return set_error(MD_ERR_INVALID, "forces need atoms");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(dL_dV_out, 0, H.N * sizeof(double), s);
+    if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    FusedArgs fa{dL_dV_out, dL_drho, dL_de};
+    md_plan* pl = nullptr;
+    st = plan_create(ham, poles, nodes, opts, rho_out, e_out, nullptr, true, s, &pl, &fa);
+    if (st != MD_OK) return st;
+    if (pl->n_sys == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        plan_free(pl);
+        return MD_OK;
+    }
+    st = plan_launch(pl, s);
+    md_status st2 = MD_OK;
+    if (st == MD_OK) st2 = plan_stats(pl, s, stats);
+    plan_free(pl);
+    if (st != MD_OK) return st;
+    if (st2 == MD_ERR_CUDA || st2 == MD_ERR_INVALID || st2 == MD_ERR_TIMEOUT) return st2;
+    if (forces_out) {
+        ForceParams F;
+        for (int d = 0; d < 3; ++d) {
+            F.n[d] = H.n[d];
+            F.h[d] = H.h[d];
+            F.periodic[d] = H.periodic[d];
+        }
+        F.n_atoms = H.n_atoms;
+        F.xyz = H.atom_xyz;
+        F.depth = H.atom_depth;
+        F.sigma = H.atom_sigma;
+        F.cutoff_sigmas = H.cutoff_sigmas;
+        F.dLdV = dL_dV_out;
+        F.forces = forces_out;
+        e = launch_forces(F, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    }
+    return st2;
 }
 
 md_status md_plan_create(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,

@@ -963,6 +963,27 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
             }
         }
         __syncthreads();
+        if (P.fused_dLdV) {
+            // this system's share of dL/dV (the forward solution is the adjoint one)
+            const double aj = P.fused_a ? P.fused_a[sd.node] : 0.0;
+            const double bj = P.fused_b ? P.fused_b[sd.node] : 0.0;
+            const double2 wp = P.w[sd.pole];
+            const double cr = 2.0 * aj / P.dV + 2.0 * bj * zd.x, ci = 2.0 * bj * zd.y;
+            const double c_re = cr * wp.x - ci * wp.y, c_im = cr * wp.y + ci * wp.x;
+            for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
+                const int c = (int)fdiv((uint32_t)i, G.div_plane);
+                const int rem = i - c * G.plane;
+                const int b = (int)fdiv((uint32_t)rem, G.div_row);
+                const int a = rem - b * G.m[0];
+                const int gx = wrap_once(G.lo[0] + a, P.n[0]);
+                const int gy = wrap_once(G.lo[1] + b, P.n[1]);
+                const int gz = wrap_once(G.lo[2] + c, P.n[2]);
+                const long long gi = gx + (long long)P.n[0] * (gy + (long long)P.n[1] * gz);
+                const double2 xv = x[i];
+                const double sq_re = xv.x * xv.x - xv.y * xv.y, sq_im = 2.0 * xv.x * xv.y;
+                atomicAdd(P.fused_dLdV + gi, -(c_re * sq_im + c_im * sq_re));
+            }
+        }
         if (P.multishift) {
             for (int k = threadIdx.x; k < P.P; k += blockDim.x) {
                 const long long o = (long long)sd.node * P.P + k;

@@ -67,6 +67,12 @@ struct SolveParams {
     int n_max;                      // vector length per slot (rounded up)
     int zm_m0, zm_m1;               // z-march kernel: largest region extents in x, y
     int multishift;                 // 1: one shifted-COCG sequence per node (work items are nodes)
+    // fused adjoint: when fused_dLdV != NULL every converged system adds
+    // -Im((2 a_j/dV + 2 b_j z_p) w_p x(k)^2) to fused_dLdV[g(k)]
+    double* fused_dLdV;
+    const double* fused_a;          // dL/drho per node, or NULL (= 0)
+    const double* fused_b;          // dL/de per node, or NULL (= 0)
+    const double2* w;               // pole weights
     double2* ckpt;                  // NULL or checkpoint base
     const long long* ckpt_sys_off;  // point offset of system (node*P + pole) in ckpt
     unsigned int* work_counter;
