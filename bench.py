@@ -37,6 +37,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "(node,pole) solves/sec and density nodes/sec at rel err<=1e-6; matvec HBM GB/s"
 BYTES_PER_POINT_ITER = {"mixed": 80.0, "fp64": 160.0}
+# DRAM bytes (read + write) per region-point iteration of the solver kernel,
+# from one ncu capture (summary under profiles/, kernel k_cocg, bulk
+# workload, 19 nodes x 16 poles, 150-iteration cap), scaled to a full launch
+# by its region-point iterations.  Valid only for the kernel sources with the
+# fingerprint below; any change to them makes the figure stale (null).
+TRAFFIC_PER_POINT_ITER = {"mixed": 71.25}
+TRAFFIC_SOURCES = ("paper_1907_02604_gb300/csrc/md_solver.cu", "paper_1907_02604_gb300/csrc/md_solver.h",
+                   "paper_1907_02604_gb300/csrc/md_device.cuh", "paper_1907_02604_gb300/csrc/md_internal.h")
+TRAFFIC_FINGERPRINT = "46e1e2f283a5251e:3cfa4a58ef899e74:6685de8068da134b:8141b58091ef73d1"
 FLOPS_PER_POINT_ITER_8TH = 200.0
 
 
@@ -56,7 +65,17 @@ def parse():
     ap.add_argument("--maxit", type=int, default=0, help="iteration cap (profiling runs)")
     ap.add_argument("--method", default="cocg", choices=["cocg", "shifted"])
     ap.add_argument("--no-shifted", action="store_true", help="skip the shifted-COCG side measurement")
+    ap.add_argument("--no-fp64-form", action="store_true", help="skip the FP64-form side measurement")
     return ap.parse_args()
+
+
+def kernel_fingerprint():
+    import hashlib
+    parts = []
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            parts.append(hashlib.sha256(fh.read()).hexdigest()[:16])
+    return ":".join(parts)
 
 
 def read_peaks():
@@ -270,14 +289,17 @@ def main():
     conv = sum(s["n_converged"] for s in stats)
     B = BYTES_PER_POINT_ITER[prec]
     achieved = point_iters * B / (kernel_ms / 1e3) / 1e9
+    traffic = None
+    if prec in TRAFFIC_PER_POINT_ITER and kernel_fingerprint() == TRAFFIC_FINGERPRINT:
+        traffic = TRAFFIC_PER_POINT_ITER[prec] * point_iters / len(stats)   # bytes per launch
     peak, peak_kind = read_peaks()
     shape = plans[0].launch_shape()
 
-    # ---- side measurement: shifted COCG (one Krylov sequence per node) -----
-    shifted = None
-    if args.method == "cocg" and not args.no_shifted:
-        from dataclasses import replace as _replace
-        sopts = _replace(opts, method="shifted", block=0, ctas_per_sm=0)
+    from dataclasses import replace as _replace
+
+    def side(sopts, note):
+        """The same steps with other solver options; density compared with
+        the timed run's on the same batches."""
         splans = [Plan(ham, z, wt, *batch(i), sopts, energy=True, stream=stream) for i in range(n_plans)]
         for i in range(args.warmup):
             splans[i % n_plans].launch(stream)
@@ -292,13 +314,29 @@ def main():
         torch.cuda.synchronize()
         sms = s0.elapsed_time(s1)
         sst = [splans[(args.warmup + i) % n_plans].stats(stream, strict=False) for i in range(args.steps)]
-        shifted = {"value": sum(x["n_systems"] for x in sst) * world / (sms / 1e3), "unit": "solves/s",
-                   "ms_per_step": sms / args.steps,
-                   "converged": f"{sum(x['n_converged'] for x in sst)}/{sum(x['n_systems'] for x in sst)}",
-                   "point_iters_per_s": sum(x["total_point_iters"] for x in sst) * world / (sms / 1e3),
-                   "note": "method 1: per node one Krylov sequence serves all poles (density only)"}
+        diff = 0.0
+        for i in range(args.steps):
+            a = splans[(args.warmup + i) % n_plans].rho
+            b = plan_of(args.warmup + i).rho
+            diff = max(diff, float((a - b).abs().max() / b.abs().max()))
+        out = {"value": sum(x["n_systems"] for x in sst) * world / (sms / 1e3), "unit": "solves/s",
+               "ms_per_step": sms / args.steps,
+               "converged": f"{sum(x['n_converged'] for x in sst)}/{sum(x['n_systems'] for x in sst)}",
+               "point_iters_per_s": sum(x["total_point_iters"] for x in sst) * world / (sms / 1e3),
+               "max_rel_diff_rho_vs_timed": diff, "note": note}
         for sp in splans:
             sp.close()
+        return out
+
+    # ---- side measurements: shifted COCG, and the plain FP64 form ----------
+    shifted = fp64_form = None
+    if args.method == "cocg" and not args.no_shifted:
+        shifted = side(_replace(opts, method="shifted", block=0, ctas_per_sm=0),
+                       "method 1: per node one Krylov sequence serves all poles (density only)")
+    if prec == "mixed" and not args.no_fp64_form:
+        fp64_form = side(_replace(opts, precision="fp64", block=0, ctas_per_sm=0),
+                         "per-pole COCG with FP64 vectors; speedup = value / this value")
+        fp64_form["speedup_mixed_over_fp64"] = value / fp64_form["value"]
 
     # ---- end to end through the C ABI from host buffers -------------------
     e2e = None
@@ -365,12 +403,14 @@ def main():
         "iters_mean": float(np.mean([s["iters_mean"] for s in stats])),
         "point_iters_per_s": point_iters * world / (el_ms / 1e3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": point_iters * B / len(stats),
                      "kernel": "k_cocg<MixedMode>" if prec == "mixed" else "k_cocg<FP64Mode>",
                      "bytes_per_point_iter": B, "peak_kind": peak_kind},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "shifted_cocg": shifted,
+        "fp64_form": fp64_form,
         "gpu_launches": 2 * args.steps,
         "launch_shape": {"threads_per_cta": shape[0], "ctas": shape[1]},
         "clocks": clocks,
