@@ -20,4 +20,7 @@ solved by COCG.  Modules:
                   spectral bounds, restriction to a region
 * ``cocg.c``      plain C FP64 COCG on one region (OpenMP over systems)
 * ``density``     nodal density, band energy, adjoint and forces
+* ``lssgq``       the paper's Lanczos spectral Gauss quadrature (Eq. 9):
+                  per-node Gauss rules, rho / band energy / entropy per node,
+                  electron count and Fermi level (Eq. Fermi:Rho)
 """
