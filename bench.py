@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--method", default="cocg", choices=["cocg", "shifted"])
     ap.add_argument("--no-shifted", action="store_true", help="skip the shifted-COCG side measurement")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the FP64-form side measurement")
+    ap.add_argument("--no-lssgq", action="store_true", help="skip the Lanczos-quadrature side measurement")
     return ap.parse_args()
 
 
@@ -338,6 +339,33 @@ def main():
                          "per-pole COCG with FP64 vectors; speedup = value / this value")
         fp64_form["speedup_mixed_over_fp64"] = value / fp64_form["value"]
 
+    # ---- side measurement: the paper's Lanczos quadrature (Eq. 9, K = 40) --
+    lssgq = None
+    if not args.no_lssgq:
+        from paper_1907_02604_gb300 import lssgq_rules
+        K = 40
+
+        def lssgq_step(i):
+            nd, hw = batch(i)
+            R = lssgq_rules(ham, nd, hw, K=K, stream=stream)
+            R.fields(w.mu, w.kT, stream=stream)
+            return R
+
+        for i in range(args.warmup):
+            lssgq_step(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rules = [lssgq_step(args.warmup + i) for i in range(args.steps)]
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        pts = sum(int(np.sum((2 * batch(args.warmup + i)[1].astype(np.int64) + 1) ** 3)) for i in range(args.steps))
+        steps_taken = sum(int(R.k_used.sum()) for R in rules)
+        lssgq = {"value": sum(R.n_nodes for R in rules) * world / el, "unit": "density nodes/s",
+                 "K": K, "ms_per_step": 1e3 * el / args.steps,
+                 "point_iters_per_s": pts * K * world / el, "lanczos_steps": steps_taken,
+                 "note": "Lanczos Gauss rules (FP64) + fields at (mu, kT); host-timed, includes the "
+                         "per-call work-list upload and status read-back"}
+
     # ---- end to end through the C ABI from host buffers -------------------
     e2e = None
     if not args.no_e2e:
@@ -411,6 +439,7 @@ def main():
         "e2e": e2e,
         "shifted_cocg": shifted,
         "fp64_form": fp64_form,
+        "lssgq": lssgq,
         "gpu_launches": 2 * args.steps,
         "launch_shape": {"threads_per_cta": shape[0], "ctas": shape[1]},
         "clocks": clocks,

@@ -325,6 +325,60 @@ md_status md_density_noalloc(const md_hamiltonian* ham, const md_poles* poles,
                              const md_nodes* nodes, const md_solver_opts* opts,
                              double* rho_out, double* e_out, md_stats* stats, void* stream);
 
+/* ---- Lanczos spectral Gauss quadrature (LSSGQ) -------------------------
+ * The paper's own route to the nodal fields (Section 2.1, Eq. 9): for node j
+ * the spectral measure of H_R(j) contracted with e_j is replaced by a
+ * K-point Gauss rule from K steps of the symmetric Lanczos process started
+ * at e_j (FP64, no reorthogonalisation); the rule's nodes lambda_jk are the
+ * eigenvalues of the Lanczos tridiagonal matrix and its weights w_jk the
+ * squared first components of its unit eigenvectors.  The rules do not
+ * depend on the Fermi level, so the fields at any (mu, kT) and the Fermi
+ * level itself (Eq. Fermi:Rho) follow without another pass over H. */
+#define MD_LSSGQ_MAX_K 128
+typedef struct {
+    int32_t K;             /* rule size = Lanczos steps, 1..MD_LSSGQ_MAX_K (paper: 40) */
+    double breakdown_tol;  /* stop early when beta_k <= tol (|alpha_1| + beta_1 + 1),
+                              the Krylov space being invariant (0 = 1e-13) */
+    double timeout_s;      /* device wall-clock budget, 0 = none */
+    int32_t block;         /* threads per CTA, 0 = 512; multiple of 32 in 64..1024 */
+} md_lssgq_opts;
+
+/* Gauss rules of every node: lambda_out, weight_out (device, n_nodes x K
+ * doubles, row j = node j, nodes ascending; entries past k_used_j repeat
+ * the largest node with weight 0); k_used_out (device, n_nodes int32, or
+ * NULL) = Lanczos steps taken (< K after a breakdown).  Regions as in
+ * md_density.  Synchronises `stream`.  Errors: MD_ERR_INVALID (bad options,
+ * nodes or regions, a region meeting more than 256 projector atoms),
+ * MD_ERR_TIMEOUT, MD_ERR_BREAKDOWN (the tridiagonal eigensolver did not
+ * converge for a node), MD_ERR_OOM, MD_ERR_CUDA. */
+md_status md_lssgq_rules(const md_hamiltonian* ham, const md_nodes* nodes,
+                         const md_lssgq_opts* opts, double* lambda_out,
+                         double* weight_out, int32_t* k_used_out, void* stream);
+
+/* Fields from the rules at Fermi level mu and temperature kT (Eqs.
+ * Electron_density:GQ and tot, per node):
+ *   rho_j = (2/dV) sum_k w_jk g(lambda_jk)
+ *   e_j   = 2 sum_k w_jk lambda_jk g(lambda_jk)                (band term)
+ *   s_j   = -2 kT sum_k w_jk [g ln g + (1-g) ln(1-g)]         (entropy term)
+ * with g the Fermi-Dirac function of Eq. (dm).  lambda, weight: device,
+ * n_nodes x K; rho_out (device, n_nodes), e_out and s_out (device or NULL).
+ * Stream-ordered, no synchronisation. */
+md_status md_lssgq_fields(int64_t n_nodes, int32_t K, const double* lambda,
+                          const double* weight, double mu, double kT, double dV,
+                          double* rho_out, double* e_out, double* s_out, void* stream);
+
+/* Fermi level (Eq. Fermi:Rho): the mu at which
+ *   N_e(mu) = 2 sum_j nu_j sum_k w_jk g(lambda_jk; mu)
+ * equals n_electrons, by bisection on the device between the smallest node
+ * - 40 kT and the largest + 40 kT, run until the bracket stops shrinking.
+ * node_weight: device, n_nodes (nu_j = grid points node j stands for), or
+ * NULL for 1 (every grid point a node).  *mu_out and *count_out (N_e at
+ * *mu_out; may be NULL) are host doubles.  Synchronises `stream`. */
+md_status md_fermi_level(int64_t n_nodes, int32_t K, const double* lambda,
+                         const double* weight, const double* node_weight, double kT,
+                         double n_electrons, double* mu_out, double* count_out,
+                         void* stream);
+
 /* Central weights w_0..w_q (q = order/2) of d^2/dx^2 on a unit grid with
  * accuracy order `order` (even, 2..16), by Fornberg's recursion (Math.
  * Comp. 51 (1988)); the library's Laplacian is -1/2 sum_d w / h_d^2 (the

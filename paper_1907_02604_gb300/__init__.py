@@ -6,8 +6,8 @@ kernels for sm_103a, behind the C ABI of include/macrodft.h.  This package
 is the Python binding (``api``), the autograd wrapper (``torch_api``) and
 the in-tree build (``build``).
 """
-from .api import (Hamiltonian, Plan, SolverOptions, Workspace, density, density_adjoint,
-                  density_fused_adjoint, energy, fd_weights, make_poles)
+from .api import (GaussRules, Hamiltonian, Plan, SolverOptions, Workspace, density, density_adjoint,
+                  density_fused_adjoint, energy, fd_weights, lssgq_rules, make_poles)
 
-__all__ = ["Hamiltonian", "Plan", "SolverOptions", "Workspace", "density", "density_adjoint",
-           "density_fused_adjoint", "energy", "fd_weights", "make_poles"]
+__all__ = ["GaussRules", "Hamiltonian", "Plan", "SolverOptions", "Workspace", "density", "density_adjoint",
+           "density_fused_adjoint", "energy", "fd_weights", "lssgq_rules", "make_poles"]

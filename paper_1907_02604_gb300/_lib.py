@@ -53,6 +53,11 @@ class md_solver_opts(ctypes.Structure):
                 ("method", ctypes.c_int32)]
 
 
+class md_lssgq_opts(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("breakdown_tol", ctypes.c_double), ("timeout_s", ctypes.c_double),
+                ("block", ctypes.c_int32)]
+
+
 class md_stats(ctypes.Structure):
     _fields_ = [("n_systems", ctypes.c_int64), ("n_converged", ctypes.c_int64),
                 ("n_noconv", ctypes.c_int64), ("n_breakdown", ctypes.c_int64),
@@ -104,6 +109,12 @@ SIGNATURES = [
                                           ctypes.POINTER(md_solver_opts), _VP, _VP,
                                           ctypes.POINTER(md_stats), _VP]),
     ("md_fd_weights", ctypes.c_int, [ctypes.c_int32, c_double_p]),
+    ("md_lssgq_rules", ctypes.c_int, [_VP, ctypes.POINTER(md_nodes), ctypes.POINTER(md_lssgq_opts),
+                                      _VP, _VP, _VP, _VP]),
+    ("md_lssgq_fields", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _VP, _VP, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP]),
+    ("md_fermi_level", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_double,
+                                      ctypes.c_double, c_double_p, c_double_p, _VP]),
     ("md_last_error", ctypes.c_char_p, []),
     ("md_version", ctypes.c_char_p, []),
 ]

@@ -343,3 +343,57 @@ def density_adjoint(ham: Hamiltonian, z, w, nodes, halfwidth, dL_drho: torch.Ten
                                     None if F is None else ctypes.c_void_p(F.data_ptr()),
                                     ctypes.byref(st), _stream_handle(stream)), "md_density_adjoint")
     return g, (F.view(-1, 3) if F is not None else None)
+
+
+class GaussRules:
+    """Per-node Lanczos Gauss rules (md_lssgq_rules): lam, weight (device,
+    n_nodes x K, float64), k_used (device, int32), dV of the grid."""
+
+    def __init__(self, lam: torch.Tensor, weight: torch.Tensor, k_used: torch.Tensor, dV: float):
+        self.lam, self.weight, self.k_used, self.dV = lam, weight, k_used, dV
+
+    @property
+    def n_nodes(self) -> int:
+        return self.lam.shape[0]
+
+    @property
+    def K(self) -> int:
+        return self.lam.shape[1]
+
+    def fields(self, mu: float, kT: float, stream=None):
+        """rho_j, e_j (band term) and s_j (entropy term) at (mu, kT)."""
+        n = self.n_nodes
+        rho = torch.empty(n, dtype=torch.float64, device="cuda")
+        e = torch.empty(n, dtype=torch.float64, device="cuda")
+        s = torch.empty(n, dtype=torch.float64, device="cuda")
+        vp = lambda t: ctypes.c_void_p(t.data_ptr())
+        check(load().md_lssgq_fields(n, self.K, vp(self.lam), vp(self.weight), float(mu), float(kT),
+                                     float(self.dV), vp(rho), vp(e), vp(s), _stream_handle(stream)),
+              "md_lssgq_fields")
+        return rho, e, s
+
+    def fermi_level(self, kT: float, n_electrons: float, node_weight: torch.Tensor = None, stream=None):
+        """(mu, N_e(mu)) with N_e(mu) = n_electrons (Eq. Fermi:Rho)."""
+        nu = None if node_weight is None else _cuda_f64(node_weight, self.n_nodes, "node_weight")
+        mu = ctypes.c_double(0.0)
+        cnt = ctypes.c_double(0.0)
+        check(load().md_fermi_level(self.n_nodes, self.K, ctypes.c_void_p(self.lam.data_ptr()),
+                                    ctypes.c_void_p(self.weight.data_ptr()),
+                                    None if nu is None else ctypes.c_void_p(nu.data_ptr()),
+                                    float(kT), float(n_electrons), ctypes.byref(mu), ctypes.byref(cnt),
+                                    _stream_handle(stream)), "md_fermi_level")
+        return mu.value, cnt.value
+
+
+def lssgq_rules(ham: Hamiltonian, nodes, halfwidth, K: int = 40, breakdown_tol: float = 0.0,
+                timeout_s: float = 0.0, block: int = 0, stream=None) -> GaussRules:
+    """K-point Lanczos Gauss rules of every node (Section 2.1, Eq. 9)."""
+    na = _NodeArgs(nodes, halfwidth)
+    lam = torch.empty((na.n, K), dtype=torch.float64, device="cuda")
+    wt = torch.empty((na.n, K), dtype=torch.float64, device="cuda")
+    ku = torch.empty(na.n, dtype=torch.int32, device="cuda")
+    o = _lib.md_lssgq_opts(int(K), float(breakdown_tol), float(timeout_s), int(block))
+    check(load().md_lssgq_rules(ham.handle, ctypes.byref(na.c), ctypes.byref(o), ctypes.c_void_p(lam.data_ptr()),
+                                ctypes.c_void_p(wt.data_ptr()), ctypes.c_void_p(ku.data_ptr()),
+                                _stream_handle(stream)), "md_lssgq_rules")
+    return GaussRules(lam, wt, ku, ham.dV)

@@ -15,6 +15,7 @@
 
 #include "md_adjoint.h"
 #include "md_internal.h"
+#include "md_lanczos.h"
 #include "md_solver.h"
 
 namespace md {
@@ -383,6 +384,38 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
     return MD_OK;
 }
 
+// Grid, stencil, potential and projector fields of the solver parameters.
+void fill_operator(SolveParams& P, const Ham& H) {
+    for (int d = 0; d < 3; ++d) {
+        P.n[d] = H.n[d];
+        P.periodic[d] = H.periodic[d];
+        for (int o = 0; o < kMaxQ; ++o) P.coef[d][o] = H.coef[d][o];
+    }
+    P.N = H.N;
+    P.q = H.q;
+    P.diag = H.diag;
+    P.dV = H.dV;
+    P.V = H.V;
+    P.V32 = H.V32;
+    P.nonlocal = H.nonlocal && H.n_atoms > 0;
+    P.n_atoms = H.n_atoms;
+    P.proj_i0 = H.proj_i0;
+    P.proj_len = H.proj_len;
+    P.proj_d = H.proj_d;
+    P.proj_g = H.proj_g;
+    P.proj_d32 = H.proj_d32;
+    P.proj_g32 = H.proj_g32;
+    P.proj_C = H.proj_C;
+    P.proj_C32 = H.proj_C32;
+    P.proj_rows = H.proj_rows;
+    P.pl_ptr = H.pl_ptr;
+    P.pl_atom = H.pl_atom;
+    P.pl_val32 = H.pl_val32;
+    P.pl_val64 = H.pl_val64;
+    P.e_s = H.e_s;
+    P.e_p = H.e_p;
+}
+
 struct FusedArgs {
     double* dLdV;
     const double* a;
@@ -493,34 +526,7 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     }
 
     SolveParams& P = pl->P;
-    for (int d = 0; d < 3; ++d) {
-        P.n[d] = H.n[d];
-        P.periodic[d] = H.periodic[d];
-        for (int o = 0; o < kMaxQ; ++o) P.coef[d][o] = H.coef[d][o];
-    }
-    P.N = H.N;
-    P.q = H.q;
-    P.diag = H.diag;
-    P.dV = H.dV;
-    P.V = H.V;
-    P.V32 = H.V32;
-    P.nonlocal = H.nonlocal && H.n_atoms > 0;
-    P.n_atoms = H.n_atoms;
-    P.proj_i0 = H.proj_i0;
-    P.proj_len = H.proj_len;
-    P.proj_d = H.proj_d;
-    P.proj_g = H.proj_g;
-    P.proj_d32 = H.proj_d32;
-    P.proj_g32 = H.proj_g32;
-    P.proj_C = H.proj_C;
-    P.proj_C32 = H.proj_C32;
-    P.proj_rows = H.proj_rows;
-    P.pl_ptr = H.pl_ptr;
-    P.pl_atom = H.pl_atom;
-    P.pl_val32 = H.pl_val32;
-    P.pl_val64 = H.pl_val64;
-    P.e_s = H.e_s;
-    P.e_p = H.e_p;
+    fill_operator(P, H);
     P.n_sys = (int)n_work;
     P.multishift = ms ? 1 : 0;
     P.w = pl->d_w;
@@ -949,6 +955,171 @@ extern "C" md_status md_density_noalloc(const md_hamiltonian* ham, const md_pole
 using namespace md;
 
 extern "C" {
+
+// ---- Lanczos spectral Gauss quadrature ------------------------------------
+
+extern "C" md_status md_lssgq_rules(const md_hamiltonian* ham, const md_nodes* nodes,
+                                    const md_lssgq_opts* opts, double* lambda_out, double* weight_out,
+                                    int32_t* k_used_out, void* stream) {
+    using namespace md;
+    clear_error();
+    md_status st = check_device();
+    if (st != MD_OK) return st;
+    if (!ham || !opts) return set_error(MD_ERR_INVALID, "ham and opts are required");
+    const int K = opts->K;
+    if (K < 1 || K > kMaxLanczosK) return set_error(MD_ERR_INVALID, "opts.K must be in 1..MD_LSSGQ_MAX_K");
+    if (!(opts->breakdown_tol >= 0.0) || !(opts->timeout_s >= 0.0))
+        return set_error(MD_ERR_INVALID, "opts: breakdown_tol and timeout_s must be >= 0");
+    if (opts->block != 0 && (opts->block < 64 || opts->block > 1024 || opts->block % 32))
+        return set_error(MD_ERR_INVALID, "opts.block must be 0 or a multiple of 32 in 64..1024");
+    Ham& H = const_cast<md_hamiltonian*>(ham)->h;
+    Regions R;
+    if ((st = make_regions(H, nodes, R)) != MD_OK) return st;
+    const long long nn = (long long)R.desc.size();
+    if (nn == 0) return MD_OK;
+    if (!lambda_out || !weight_out) return set_error(MD_ERR_INVALID, "lambda_out and weight_out are required");
+    if (nn > (1LL << 31) - 1) return set_error(MD_ERR_INVALID, "too many nodes");
+    cudaStream_t s = (cudaStream_t)stream;
+
+    std::vector<SysDesc> sys(nn);
+    for (long long j = 0; j < nn; ++j) sys[j] = SysDesc{(int)j, 0};
+    std::stable_sort(sys.begin(), sys.end(),
+                     [&](const SysDesc& a, const SysDesc& b) { return R.points[a.node] > R.points[b.node]; });
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int block = opts->block > 0 ? opts->block : 512;
+    const int per_sm = std::max(1, std::min(2, 1024 / block));
+    const int grid = (int)std::min<long long>((long long)n_sm * per_sm, nn);
+
+    SolveParams P;
+    std::memset(&P, 0, sizeof(P));
+    fill_operator(P, H);
+    P.n_sys = (int)nn;
+    P.timeout_ns = opts->timeout_s > 0 ? (unsigned long long)(opts->timeout_s * 1e9) : 0ULL;
+    P.n_max = (int)((R.n_max + 63) / 64 * 64);
+    P.slot_bytes = ((size_t)2 * P.n_max * sizeof(double) + 511) / 512 * 512;
+
+    SysDesc* d_sys = nullptr;
+    NodeDesc* d_nodes = nullptr;
+    double *d_alpha = nullptr, *d_beta = nullptr;
+    int *d_kused = nullptr, *d_status = nullptr;
+    unsigned int* d_counter = nullptr;
+    auto release = [&]() {
+        cudaFree(d_sys);
+        cudaFree(d_nodes);
+        cudaFree(d_alpha);
+        cudaFree(d_beta);
+        cudaFree(d_kused);
+        cudaFree(d_status);
+        cudaFree(d_counter);
+    };
+#define LTRY(expr)                                                                                   \
+    do {                                                                                             \
+        cudaError_t _e = (expr);                                                                     \
+        if (_e != cudaSuccess) {                                                                     \
+            release();                                                                               \
+            return set_error((_e == cudaErrorMemoryAllocation) ? MD_ERR_OOM : MD_ERR_CUDA,           \
+                             std::string("CUDA: ") + cudaGetErrorString(_e) + " (" #expr ")");       \
+        }                                                                                            \
+    } while (0)
+    const size_t need = P.slot_bytes * (size_t)grid;
+    if (need > H.scratch_bytes) {
+        LTRY(cudaStreamSynchronize(s));
+        if (H.scratch) cudaFree(H.scratch);
+        H.scratch = nullptr;
+        H.scratch_bytes = 0;
+        LTRY(cudaMalloc(&H.scratch, need));
+        H.scratch_bytes = need;
+    }
+    P.scratch = (char*)H.scratch;
+    LTRY(cudaMalloc(&d_sys, nn * sizeof(SysDesc)));
+    LTRY(cudaMalloc(&d_nodes, nn * sizeof(NodeDesc)));
+    LTRY(cudaMalloc(&d_alpha, nn * K * sizeof(double)));
+    LTRY(cudaMalloc(&d_beta, nn * K * sizeof(double)));
+    LTRY(cudaMalloc(&d_kused, nn * sizeof(int)));
+    LTRY(cudaMalloc(&d_status, nn * sizeof(int)));
+    LTRY(cudaMalloc(&d_counter, sizeof(unsigned int)));
+    LTRY(cudaMemcpyAsync(d_sys, sys.data(), nn * sizeof(SysDesc), cudaMemcpyHostToDevice, s));
+    LTRY(cudaMemcpyAsync(d_nodes, R.desc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, s));
+    LTRY(cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), s));
+    LTRY(cudaMemsetAsync(d_kused, 0, nn * sizeof(int), s));
+    P.sys = d_sys;
+    P.nodes = d_nodes;
+    P.work_counter = d_counter;
+    LanczosParams L;
+    L.K = K;
+    L.breakdown_tol = opts->breakdown_tol > 0 ? opts->breakdown_tol : 1e-13;
+    L.alpha = d_alpha;
+    L.beta = d_beta;
+    L.k_used = d_kused;
+    L.status = d_status;
+    LTRY(launch_lanczos(P, L, grid, block, s));
+    LTRY(launch_gauss_rules((int)nn, L, lambda_out, weight_out, s));
+    if (k_used_out)
+        LTRY(cudaMemcpyAsync(k_used_out, d_kused, nn * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    std::vector<int> h_status(nn);
+    LTRY(cudaMemcpyAsync(h_status.data(), d_status, nn * sizeof(int), cudaMemcpyDeviceToHost, s));
+    LTRY(cudaStreamSynchronize(s));
+#undef LTRY
+    release();
+    int worst = 0;
+    for (int v : h_status) worst = (v == 4 || worst == 4) ? 4 : std::max(worst, v);
+    if (worst == 4) return set_error(MD_ERR_TIMEOUT, "device time budget exhausted; rules incomplete");
+    if (worst == 1)
+        return set_error(MD_ERR_INVALID, "a region meets more projector atoms than the solver holds (256)");
+    if (worst == 3) return set_error(MD_ERR_BREAKDOWN, "the tridiagonal QR did not converge for some node");
+    return MD_OK;
+}
+
+extern "C" md_status md_lssgq_fields(int64_t n_nodes, int32_t K, const double* lambda, const double* weight,
+                                     double mu, double kT, double dV, double* rho_out, double* e_out,
+                                     double* s_out, void* stream) {
+    using namespace md;
+    clear_error();
+    md_status st = check_device();
+    if (st != MD_OK) return st;
+    if (n_nodes < 0 || n_nodes > (1LL << 31) - 1 || K < 1 || K > kMaxLanczosK)
+        return set_error(MD_ERR_INVALID, "n_nodes or K out of range");
+    if (!(kT > 0.0) || !(dV > 0.0) || !std::isfinite(mu))
+        return set_error(MD_ERR_INVALID, "kT and dV must be > 0 and mu finite");
+    if (n_nodes == 0) return MD_OK;
+    if (!lambda || !weight || !rho_out) return set_error(MD_ERR_INVALID, "lambda, weight and rho_out are required");
+    cudaError_t e = launch_lssgq_fields((int)n_nodes, K, lambda, weight, mu, kT, dV, rho_out, e_out, s_out,
+                                        (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    return MD_OK;
+}
+
+extern "C" md_status md_fermi_level(int64_t n_nodes, int32_t K, const double* lambda, const double* weight,
+                                    const double* node_weight, double kT, double n_electrons, double* mu_out,
+                                    double* count_out, void* stream) {
+    using namespace md;
+    clear_error();
+    md_status st = check_device();
+    if (st != MD_OK) return st;
+    if (n_nodes < 1 || n_nodes > (1LL << 31) - 1 || K < 1 || K > kMaxLanczosK)
+        return set_error(MD_ERR_INVALID, "n_nodes or K out of range");
+    if (!(kT > 0.0) || !(n_electrons >= 0.0) || !std::isfinite(n_electrons))
+        return set_error(MD_ERR_INVALID, "kT must be > 0 and n_electrons finite and >= 0");
+    if (!lambda || !weight || !mu_out) return set_error(MD_ERR_INVALID, "lambda, weight and mu_out are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    double* d_out = nullptr;
+    cudaError_t e = cudaMalloc(&d_out, 3 * sizeof(double));
+    if (e == cudaSuccess) e = launch_fermi_level((int)n_nodes, K, lambda, weight, node_weight, kT, n_electrons,
+                                                 d_out, s);
+    double h[3] = {0.0, 0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_out);
+    if (e != cudaSuccess)
+        return set_error(e == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA,
+                         std::string("CUDA: ") + cudaGetErrorString(e));
+    *mu_out = h[0];
+    if (count_out) *count_out = h[1];
+    return MD_OK;
+}
+
 
 const char* md_last_error(void) { return md::g_last_error.c_str(); }
 
