@@ -37,12 +37,31 @@ class OracleHamiltonian:
     emax: float
 
 
-def build(w) -> OracleHamiltonian:
-    V = ham_mod.local_potential(w)
+def build(w, points=None, bounds=None) -> OracleHamiltonian:
+    """The Hamiltonian of workload w.  With `points` (flat grid indices, or
+    a list of such arrays, e.g. one per region to be solved) V is computed
+    there only (zero elsewhere) and the spectral interval must be given as
+    `bounds` = (emin, emax), since Gershgorin needs V on the whole grid."""
     projs = ham_mod.projectors(w)
     st = ham_mod.kinetic_stencil(w.spacing, w.fd_order)
-    emin, emax = ham_mod.gershgorin_bounds(w, V, projs)
-    return OracleHamiltonian(V=V, projs=projs, stencil=st, emin=emin, emax=emax)
+    if points is None:
+        V = ham_mod.local_potential(w)
+        emin, emax = ham_mod.gershgorin_bounds(w, V, projs) if bounds is None else bounds
+    else:
+        if bounds is None:
+            raise ValueError("a restricted build needs explicit spectral bounds")
+        V = np.zeros(w.n_grid)
+        chunks = points if isinstance(points, (list, tuple)) else [points]
+        for c in chunks:   # one region at a time keeps each atom filter local
+            pts = np.unique(np.asarray(c, dtype=np.int64))
+            V[pts] = ham_mod.local_potential_on(w, pts)
+        emin, emax = bounds
+    return OracleHamiltonian(V=V, projs=projs, stencil=st, emin=float(emin), emax=float(emax))
+
+
+def region_points(w) -> list:
+    """The grid points of every node's region, one array per node."""
+    return [ham_mod.region_of(w, int(n), int(s)).gidx for n, s in zip(w.nodes, w.halfwidth)]
 
 
 def poles_for(w, H: OracleHamiltonian):
@@ -151,6 +170,14 @@ def solve(w, H: OracleHamiltonian = None, z=None, wts=None, tol: float = 1e-12,
                         z=z, wts=wts, regions=regions, x_full=xf)
 
 
+def density_matrix_rows(res: OracleResult) -> list:
+    """Row j of the density matrix over R(j) (Eq. dm in the grid basis, g
+    replaced by r): gamma_jk = sum_p Im(w_p x_jp(k)); rho_j = (2/dV) gamma_jj."""
+    if res.x_full is None:
+        raise ValueError("solve with keep_x=True first")
+    return [np.imag((res.wts[:, None] * xf).sum(axis=0)) for xf in res.x_full]
+
+
 def dL_dV(w, res: OracleResult, a_node, b_node=None) -> np.ndarray:
     """Gradient of L with respect to the local potential on the grid."""
     if res.x_full is None:
@@ -165,10 +192,12 @@ def dL_dV(w, res: OracleResult, a_node, b_node=None) -> np.ndarray:
     return g
 
 
-def forces(w, dLdV: np.ndarray) -> np.ndarray:
-    """F_a = -sum_k dL/dV_k dV_k/dR_a (local Gaussian wells only)."""
-    F = np.zeros((len(w.atoms), 3))
-    for a in range(len(w.atoms)):
-        gidx, dVdR = ham_mod.local_potential_gradient_terms(w, a)
-        F[a] = -(dLdV[gidx][:, None] * dVdR).sum(axis=0)
+def forces(w, dLdV: np.ndarray, atoms=None) -> np.ndarray:
+    """F_a = -sum_k dL/dV_k dV_k/dR_a (local Gaussian wells only), for every
+    atom or for the listed ones (rows in that order)."""
+    sel = np.arange(len(w.atoms)) if atoms is None else np.asarray(atoms, dtype=np.int64)
+    F = np.zeros((len(sel), 3))
+    for i, a in enumerate(sel):
+        gidx, dVdR = ham_mod.local_potential_gradient_terms(w, int(a))
+        F[i] = -(dLdV[gidx][:, None] * dVdR).sum(axis=0)
     return F

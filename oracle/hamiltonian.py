@@ -99,6 +99,42 @@ def local_potential(w) -> np.ndarray:
     return V.reshape(-1) + np.asarray(w.v_ext, dtype=np.float64)
 
 
+def local_potential_on(w, gidx) -> np.ndarray:
+    """V at the grid points gidx only (flat indices, x fastest): the same sum
+    of wells as local_potential plus v_ext there, for grids too large to
+    fill whole.  Atoms farther than the cutoff from the points' bounding box
+    (minimum image on periodic axes) are skipped before the per-atom sum."""
+    nx, ny, _ = w.shape
+    gidx = np.asarray(gidx, dtype=np.int64)
+    idx = (gidx % nx, (gidx // nx) % ny, gidx // (nx * ny))
+    coords = [idx[d] * w.spacing[d] for d in range(3)]
+    box = w.box
+    lo = np.array([c.min() for c in coords])
+    hi = np.array([c.max() for c in coords])
+    mid, half = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    rc_all = w.cutoff_sigmas * np.asarray(w.sigma, dtype=np.float64)
+    near = np.ones(len(w.atoms), dtype=bool)
+    for d in range(3):
+        dd = w.atoms[:, d] - mid[d]
+        if w.periodic[d]:
+            dd = dd - box[d] * np.round(dd / box[d])
+        near &= np.abs(dd) <= half[d] + rc_all
+    V = np.zeros(len(gidx))
+    for a in np.nonzero(near)[0]:
+        R = w.atoms[a]
+        sig = float(w.sigma[a])
+        rc = rc_all[a]
+        r2 = np.zeros(len(gidx))
+        for d in range(3):
+            dd = coords[d] - R[d]
+            if w.periodic[d]:
+                dd = dd - box[d] * np.round(dd / box[d])
+            r2 += dd * dd
+        m = r2 <= rc * rc
+        V[m] += -float(w.depth[a]) * np.exp(-r2[m] / (2.0 * sig * sig))
+    return V + np.asarray(w.v_ext, dtype=np.float64)[gidx]
+
+
 def local_potential_gradient_terms(w, a: int):
     """Grid points touched by atom a and dV_k/dR_a (3 columns) there."""
     R = w.atoms[a]

@@ -293,6 +293,77 @@ def screw_batched() -> Workload:
               "d0": d0, "ell": ell, "box": box})
 
 
+def large_loop(n_atoms: int = 100_000, nz_cells: int = 24, n_nodes: int = 200_000,
+               node_seed: int = 6, candidate_stride: int = 2) -> Workload:
+    """hcp cylinder of n_atoms sites (axis along c, length nz_cells c,
+    periodic in z) carrying a prismatic dislocation loop of radius R = 40
+    bohr in the plane z0 = L_z/2 around the axis, with the synthetic
+    displacement
+        u_z = -(b/2) sgn(z - z0) exp(-|z - z0|/R) sigma((R - rho)/w),
+    b = c/2, w = 2 bohr, sigma the logistic function, rho the distance to
+    the axis; the 20 sites nearest the loop-plane diameter along x (within
+    R + 10 bohr of the axis) are Al-like wells of depth 1.3 Ha.  Grid
+    h = 0.5 bohr in x, y (open, 11 bohr vacuum margin) and ~0.5 bohr in z,
+    8th order; n_nodes nodes sampled (on the sub-lattice of every
+    candidate_stride-th grid point inside the cylinder) with density
+    1/(1 + (d/8)^2), d the distance to the loop line, region half-width
+    s(d) = clamp(20 - floor(d/l), 8, 20), l = r_cyl/13; P = 16, mixed.
+    meta["force_atoms"]: the 2,000 sites nearest the loop line.
+    """
+    Lz = nz_cells * C_LAT
+    per_area = 2.0 / (0.5 * math.sqrt(3.0) * A_LAT ** 2)        # sites per bohr^2 per cell layer
+    r_est = math.sqrt(n_atoms / (nz_cells * per_area * math.pi))
+    h = 0.5
+    nxy = 2 * int(math.ceil((r_est + 4.0 + 11.0) / h))
+    nz = 2 * int(round(Lz / h / 2.0))
+    shape = (nxy, nxy, nz)
+    spacing = (h, h, Lz / nz)
+    box = (nxy * h, nxy * h, Lz)
+    x0, y0 = 0.5 * box[0], 0.5 * box[1]
+    z0 = 0.5 * Lz
+    pos = _cylinder_sites(n_atoms, nz_cells, (x0, y0))
+    R, b, wd = 40.0, 0.5 * C_LAT, 2.0
+    rho = np.hypot(pos[:, 0] - x0, pos[:, 1] - y0)
+    dz = pos[:, 2] - z0
+    uz = -0.5 * b * np.sign(dz) * np.exp(-np.abs(dz) / R) / (1.0 + np.exp(-(R - rho) / wd))
+    pos[:, 2] = np.mod(pos[:, 2] + uz, Lz)
+    r_cyl = float(np.max(np.hypot(pos[:, 0] - x0, pos[:, 1] - y0)))
+    na = len(pos)
+    depth = np.full(na, 1.0)
+    near_line = np.hypot(pos[:, 1] - y0, pos[:, 2] - z0)
+    ok = np.abs(pos[:, 0] - x0) <= R + 10.0
+    cand_al = np.nonzero(ok)[0]
+    al = cand_al[np.lexsort((cand_al, np.round(near_line[cand_al], 9)))[:20]]
+    depth[al] = 1.3
+    d_atom = np.hypot(np.hypot(pos[:, 0] - x0, pos[:, 1] - y0) - R, pos[:, 2] - z0)
+    force_atoms = np.lexsort((np.arange(na), np.round(d_atom, 9)))[:2000].astype(np.int64)
+    n_grid = int(np.prod(shape))
+    # candidate nodes: every candidate_stride-th grid point inside the cylinder
+    st = candidate_stride
+    ix, iy, iz = np.meshgrid(np.arange(0, shape[0], st), np.arange(0, shape[1], st),
+                             np.arange(0, shape[2], st), indexing="ij")
+    ix, iy, iz = ix.ravel(), iy.ravel(), iz.ravel()
+    rr = np.hypot(ix * spacing[0] - x0, iy * spacing[1] - y0)
+    keep = rr <= r_cyl
+    ix, iy, iz, rr = ix[keep], iy[keep], iz[keep], rr[keep]
+    cand = (ix + shape[0] * (iy + shape[1] * iz)).astype(np.int64)
+    d = np.hypot(rr - R, iz * spacing[2] - z0)
+    nodes = sample_weighted_nodes(cand, 1.0 / (1.0 + (d / 8.0) ** 2), min(n_nodes, len(cand)), node_seed)
+    dn = np.hypot(np.hypot((nodes % shape[0]) * spacing[0] - x0,
+                           ((nodes // shape[0]) % shape[1]) * spacing[1] - y0) - R,
+                  (nodes // (shape[0] * shape[1])) * spacing[2] - z0)
+    ell = r_cyl / 13.0
+    s = np.clip(20 - np.floor(dn / ell).astype(np.int64), 8, 20).astype(np.int32)
+    return Workload(
+        name="large_loop", shape=shape, spacing=spacing,
+        periodic=(False, False, True), fd_order=8,
+        atoms=pos, depth=depth, sigma=np.full(na, 1.2),
+        v_ext=noise_potential(n_grid), nodes=nodes, halfwidth=s,
+        n_poles=16, precision="mixed",
+        meta={"loop_center": (x0, y0, z0), "loop_radius": R, "burgers": b, "r_cyl": r_cyl,
+              "al_atoms": al.astype(np.int64), "force_atoms": force_atoms, "ell": ell, "box": box})
+
+
 def tiny(shape=(6, 6, 8), n_atoms=3, fd_order=4, s=2, n_nodes=6, seed=11,
          nonlocal_proj=False, n_poles=8, spacing=(0.55, 0.6, 0.5),
          periodic=(True, True, True)) -> Workload:
@@ -318,6 +389,7 @@ WORKLOADS = {
     "bulk_mixed": bulk_mixed,
     "screw_batched": screw_batched,
     "adjoint_fp64": adjoint_fp64,
+    "large_loop": large_loop,
 }
 
 

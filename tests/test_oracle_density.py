@@ -161,3 +161,17 @@ def test_forces_vs_finite_difference():
                 vals.append(np.dot(a, r2.rho) + np.dot(b, r2.e_node))
             fd = -(vals[0] - vals[1]) / (2 * step)
             assert abs(fd - F[atom, d]) < 1e-6 * max(1.0, np.abs(F).max())
+
+
+def test_density_matrix_rows_vs_dense():
+    """gamma_jk = sum_p Im(w_p x_jp(k)) equals row j of r(H_R) from dense
+    eigh, and its diagonal gives rho_j."""
+    w = make_workload("tiny", nonlocal_proj=True, fd_order=4, s=2, n_nodes=3)
+    H = od.build(w)
+    res = od.solve(w, H, tol=1e-13, keep_x=True)
+    rows = od.density_matrix_rows(res)
+    for j, reg in enumerate(res.regions):
+        ev, U = np.linalg.eigh(_dense_for(w, H, reg))
+        gamma = (U * rational(ev, res.z, res.wts)[None, :]) @ U[reg.src, :]
+        np.testing.assert_allclose(rows[j], gamma, atol=1e-11 * np.abs(gamma).max())
+        assert abs(2.0 / w.dV * rows[j][reg.src] - res.rho[j]) <= 1e-12 * abs(res.rho[j])

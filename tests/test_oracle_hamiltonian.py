@@ -127,3 +127,27 @@ def test_nonlocal_operator_spectrum():
     ev = np.sort(np.linalg.eigvalsh(M))[::-1]
     np.testing.assert_allclose(ev[:4], [0.5, 0.25, 0.25, 0.25], atol=1e-12)
     assert np.abs(ev[4:]).max() < 1e-12
+
+
+def test_potential_on_points_equals_full_grid():
+    """The restricted potential (large grids) is the full-grid one at the
+    same points: periodic cell, open-axis cylinder, and a restricted build
+    with given bounds keeps V there."""
+    from oracle import density as od
+    rng = np.random.default_rng(3)
+    for w in (make_workload("tiny", shape=(12, 10, 14), n_atoms=5),
+              make_workload("tiny", shape=(14, 12, 16), periodic=(False, True, False), n_atoms=4)):
+        V = H.local_potential(w)
+        idx = rng.choice(w.n_grid, size=300, replace=False)
+        np.testing.assert_allclose(H.local_potential_on(w, idx), V[idx], rtol=1e-13, atol=1e-15)
+        c = w.node_coords()
+        ok = np.ones(len(w.nodes), bool)
+        for d in range(3):
+            if not w.periodic[d]:
+                ok &= (c[:, d] - w.halfwidth >= 0) & (c[:, d] + w.halfwidth < w.shape[d])
+        ws = w.subset(np.nonzero(ok)[0][:2])
+        pts = od.region_points(ws)
+        Hr = od.build(ws, points=pts, bounds=(-3.0, 40.0))
+        for p in pts:
+            np.testing.assert_allclose(Hr.V[p], V[p], rtol=1e-13, atol=1e-15)
+        assert (Hr.emin, Hr.emax) == (-3.0, 40.0)
