@@ -232,6 +232,22 @@ md_status md_density_fused_adjoint(const md_hamiltonian* ham, const md_poles* po
                                    double* e_out, double* dL_dV_out, double* forces_out,
                                    md_stats* stats, void* stream);
 
+/* Rows of the density matrix within each region (Eq. dm in the orthonormal
+ * grid basis, g replaced by r): for node j and every region point k,
+ *     gamma_jk = sum_p Im(w_p x_jp(k)),   so that rho_j = (2/dV) gamma_jj,
+ * from the same per-pole COCG solves as md_density.  rows_out: device,
+ * sum_j |R(j)| doubles; row j starts at sum_{i<j} |R(i)| and is laid out
+ * region-local (x fastest, as the region of md_density).  Every converged
+ * system adds its pole's share with FP64 atomics (last-bit
+ * nondeterministic).  rho_out (device, n_nodes; required when n_nodes > 0)
+ * and e_out (device or NULL) as in md_energy.  opts may be NULL (mixed,
+ * tol 1e-10); method 1 is refused.  Synchronises `stream`.  Status as in
+ * md_density. */
+md_status md_density_matrix_rows(const md_hamiltonian* ham, const md_poles* poles,
+                                 const md_nodes* nodes, const md_solver_opts* opts,
+                                 double* rho_out, double* e_out, double* rows_out,
+                                 md_stats* stats, void* stream);
+
 /* ---- Plans: a prepared batched solve replayed as a CUDA graph ----------
  * md_plan_create validates the inputs once, uploads the cost-sorted
  * (node, pole) work list and region descriptors, allocates the plan's own

@@ -7,7 +7,9 @@ is the Python binding (``api``), the autograd wrapper (``torch_api``) and
 the in-tree build (``build``).
 """
 from .api import (GaussRules, Hamiltonian, Plan, SolverOptions, Workspace, density, density_adjoint,
-                  density_fused_adjoint, energy, fd_weights, lssgq_rules, make_poles)
+                  density_fused_adjoint, density_matrix_rows, energy, fd_weights, lssgq_rules,
+                  make_poles)
 
 __all__ = ["GaussRules", "Hamiltonian", "Plan", "SolverOptions", "Workspace", "density", "density_adjoint",
-           "density_fused_adjoint", "energy", "fd_weights", "lssgq_rules", "make_poles"]
+           "density_fused_adjoint", "density_matrix_rows", "energy", "fd_weights", "lssgq_rules",
+           "make_poles"]

@@ -97,6 +97,9 @@ SIGNATURES = [
     ("md_density_fused_adjoint", ctypes.c_int, [_VP, ctypes.POINTER(md_poles), ctypes.POINTER(md_nodes),
                                                 ctypes.POINTER(md_solver_opts), _VP, _VP, _VP, _VP, _VP,
                                                 _VP, ctypes.POINTER(md_stats), _VP]),
+    ("md_density_matrix_rows", ctypes.c_int, [_VP, ctypes.POINTER(md_poles), ctypes.POINTER(md_nodes),
+                                              ctypes.POINTER(md_solver_opts), _VP, _VP, _VP,
+                                              ctypes.POINTER(md_stats), _VP]),
     ("md_plan_create", ctypes.c_int, [_VP, ctypes.POINTER(md_poles), ctypes.POINTER(md_nodes),
                                       ctypes.POINTER(md_solver_opts), _VP, _VP, _VP, _VP,
                                       ctypes.POINTER(_VP)]),

@@ -85,6 +85,7 @@ class Hamiltonian:
         lib = load()
         self.shape = tuple(int(n) for n in shape)
         self.spacing = tuple(float(h) for h in spacing)
+        self.periodic = tuple(bool(p) for p in periodic)
         self.N = int(np.prod(self.shape))
         self.dV = float(np.prod(self.spacing))
         self._atoms = np.ascontiguousarray(np.asarray(atoms, dtype=np.float64).reshape(-1, 3))
@@ -321,6 +322,37 @@ def density_fused_adjoint(ham: Hamiltonian, z, w, nodes, halfwidth, dL_drho: tor
                                           ctypes.byref(st), _stream_handle(stream)),
           "md_density_fused_adjoint")
     return rho, e, g, (F.view(-1, 3) if F is not None else None), st.as_dict()
+
+
+def density_matrix_rows(ham: Hamiltonian, z, w, nodes, halfwidth, opts: SolverOptions = None,
+                        stream=None):
+    """rho, e and the density-matrix rows gamma_jk (k over R(j)) of every
+    node: returns (rho, e, rows, offsets) with row j = rows[offsets[j]:offsets[j+1]]
+    in region-local order (x fastest)."""
+    opts = opts or SolverOptions()
+    pa, na = _PoleArgs(z, w), _NodeArgs(nodes, halfwidth)
+    sizes = np.array([_region_size(ham, int(n), int(s)) for n, s in zip(na.node, na.hw)], dtype=np.int64)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    rho = torch.empty(na.n, dtype=torch.float64, device="cuda")
+    e = torch.empty(na.n, dtype=torch.float64, device="cuda")
+    rows = torch.empty(int(offsets[-1]), dtype=torch.float64, device="cuda")
+    st = _lib.md_stats()
+    copts = opts.to_c()
+    vp = lambda t: ctypes.c_void_p(t.data_ptr()) if t.numel() else None
+    check(load().md_density_matrix_rows(ham.handle, ctypes.byref(pa.c), ctypes.byref(na.c), ctypes.byref(copts),
+                                        vp(rho), vp(e), vp(rows), ctypes.byref(st), _stream_handle(stream)),
+          "md_density_matrix_rows")
+    return rho, e, rows, offsets
+
+
+def _region_size(ham: Hamiltonian, node: int, s: int) -> int:
+    """Points of the region of a node (cube of side 2s+1; whole axis on a
+    periodic axis it would cover), as the library lays it out."""
+    n = 1
+    for d in range(3):
+        m = 2 * s + 1
+        n *= ham.shape[d] if (ham.periodic[d] and m >= ham.shape[d]) else m
+    return n
 
 
 def density_adjoint(ham: Hamiltonian, z, w, nodes, halfwidth, dL_drho: torch.Tensor,

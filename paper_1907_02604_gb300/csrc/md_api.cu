@@ -218,7 +218,7 @@ struct md_plan {
     int Pn = 0;
     long long nn = 0;
     long long n_sys = 0;
-    int grid = 0, block = 0;
+    int grid = 0, block = 0, per_sm = 1;
     int variant = 0;                   // 0 generic kernel, K > 0: z-march kernel with K columns per thread
     bool multishift = false;           // one shifted-COCG work item per node
     size_t smem = 0;                   // dynamic shared memory of the z-march kernel
@@ -280,15 +280,17 @@ struct Shape {
 
 cudaError_t launch_shape(const md_plan* pl, const SolveParams& P, const Shape& sh, int grid, cudaStream_t s) {
     if (sh.variant > 0) return launch_cocg_zm(P, sh.variant, grid, sh.block, pl->smem, s);
-    return launch_cocg(P, pl->precision, grid, sh.block, s);
+    return launch_cocg(P, pl->precision, grid, sh.block, sh.per_sm, s);
 }
 
-// Candidate launch shapes: the generic kernel at 1024x1 and 512x2, and, when
-// the z-march kernel applies, K = 1..4 columns per thread with the smallest
+// Candidate launch shapes: the generic kernel at 1024x1 and 512x2 (and, in
+// mixed precision, 512x3 from its 40-register instance), and, when the
+// z-march kernel applies, K = 1..4 columns per thread with the smallest
 // warp-multiple block covering the largest plane, at every CTAs-per-SM
 // count the occupancy calculator allows.
 std::vector<Shape> candidate_shapes(const md_plan* pl, bool zm_ok, int max_plane) {
     std::vector<Shape> c = {{0, 1024, 1}, {0, 512, 2}};
+    if (pl->precision == MD_PREC_MIXED) c.push_back({0, 512, 3});
     if (!zm_ok) return c;
     for (int K = 1; K <= 4; ++K) {
         const int need = (max_plane + K - 1) / K;
@@ -328,7 +330,10 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
             return MD_OK;
         }
     const long long nw = pl->P.n_sys;   // work items (systems, or nodes with shifted COCG)
-    const long long ns = std::min<long long>(nw, n_sm);
+    int max_per = 1;
+    for (const auto& c : cands) max_per = std::max(max_per, c.per_sm);
+    // enough systems that every candidate's CTAs each take two in turn
+    const long long ns = std::min<long long>(nw, 2LL * n_sm * max_per);
     std::vector<SysDesc> all(nw), sample;
     PLAN_TRY(cudaMemcpy(all.data(), pl->d_sys, nw * sizeof(SysDesc), cudaMemcpyDeviceToHost));
     for (long long k = 0; k < ns; ++k) sample.push_back(all[(k * nw) / ns]);
@@ -342,9 +347,10 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
         SolveParams T = pl->P;
         T.sys = d_sample;
         T.n_sys = (int)ns;
-        T.maxit = std::min(pl->P.maxit, 48);
+        T.maxit = std::min(pl->P.maxit, 64);
         T.ckpt = nullptr;         // trials never touch the checkpoint
         T.fused_dLdV = nullptr;   // nor the gradient
+        T.dm_rows = nullptr;
         const int grid = (int)std::min<long long>((long long)n_sm * c.per_sm, ns);
         if (pl->P.slot_bytes * (size_t)grid > scratch_bytes) continue;
         cudaMemset(T.work_counter, 0, sizeof(unsigned int));
@@ -417,9 +423,11 @@ void fill_operator(SolveParams& P, const Ham& H) {
 }
 
 struct FusedArgs {
-    double* dLdV;
+    double* dLdV;           // fused adjoint (may be NULL)
     const double* a;
     const double* b;
+    double* dm_rows;        // density-matrix rows (may be NULL)
+    const long long* dm_off;
 };
 
 md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,
@@ -534,6 +542,8 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
         P.fused_dLdV = fused->dLdV;
         P.fused_a = fused->a;
         P.fused_b = fused->b;
+        P.dm_rows = fused->dm_rows;
+        P.dm_off = fused->dm_off;
     }
     P.P = Pn;
     P.sys = pl->d_sys;
@@ -560,8 +570,8 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     P.zm_m0 = R.max_dim[0];
     P.zm_m1 = R.max_dim[1];
     if (zm_ok) pl->smem = zm_smem_bytes(H.q, R.max_dim[0], R.max_dim[1]);
-    // scratch sized for the widest candidate (2 CTAs per SM)
-    const int max_ctas = (int)std::min<long long>((long long)n_sm * 2, n_work);
+    // scratch sized for the widest candidate (3 CTAs per SM)
+    const int max_ctas = (int)std::min<long long>((long long)n_sm * 3, n_work);
     const size_t need = P.slot_bytes * (size_t)max_ctas;
     if (borrow_scratch) {
         if (need > H.scratch_bytes) {
@@ -593,16 +603,17 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
         if (ts != MD_OK) return fail(ts);
     }
     if (shape.per_sm <= 0) shape.per_sm = std::max(1, 1024 / shape.block);
-    shape.per_sm = std::min(shape.per_sm, 2);
+    shape.per_sm = std::min(shape.per_sm, opts.precision == MD_PREC_MIXED && shape.variant == 0 ? 3 : 2);
     pl->variant = shape.variant;
     pl->block = shape.block;
+    pl->per_sm = shape.per_sm;
     pl->grid = (int)std::min<long long>((long long)n_sm * shape.per_sm, n_work);
 
     // capture [reset counter, solver, accumulation] once; launches replay it
     PTRY(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
     {
         cudaError_t e1 = cudaMemsetAsync(pl->d_counter, 0, sizeof(unsigned int), pl->cap);
-        cudaError_t e2 = launch_shape(pl, P, Shape{pl->variant, pl->block, 0}, pl->grid, pl->cap);
+        cudaError_t e2 = launch_shape(pl, P, Shape{pl->variant, pl->block, pl->per_sm}, pl->grid, pl->cap);
         cudaError_t e3 = launch_accumulate((int)nn, Pn, pl->d_xsrc, pl->d_z, pl->d_w, H.dV, rho_out, e_out, pl->cap);
         cudaError_t e4 = cudaStreamEndCapture(pl->cap, &pl->graph);
         PTRY(e1);
@@ -915,7 +926,7 @@ extern "C" md_status md_density_noalloc(const md_hamiltonian* ham, const md_pole
     // one CTA of 1024 threads per SM, as many as the slots in the array allow
     const long long max_slots = (long long)(kNaScratchBytes / slot);
     const int grid = (int)std::min<long long>(std::min<long long>(n_sm, max_slots), n_sys);
-    e = launch_cocg(P, o.precision, grid, 1024, stream);
+    e = launch_cocg(P, o.precision, grid, 1024, 1, stream);
     if (e == cudaSuccess) e = launch_accumulate((int)nn, Pn, d_xsrc, d_z, d_w, H.dV, rho_out, e_out, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g_na_status, d_status, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g_na_iters, d_iters, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream);
@@ -1434,7 +1445,7 @@ md_status md_density_fused_adjoint(const md_hamiltonian* ham, const md_poles* po
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(dL_dV_out, 0, H.N * sizeof(double), s);
     if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
-    FusedArgs fa{dL_dV_out, dL_drho, dL_de};
+    FusedArgs fa{dL_dV_out, dL_drho, dL_de, nullptr, nullptr};
     md_plan* pl = nullptr;
     st = plan_create(ham, poles, nodes, opts, rho_out, e_out, nullptr, true, s, &pl, &fa);
     if (st != MD_OK) return st;
@@ -1468,6 +1479,62 @@ md_status md_density_fused_adjoint(const md_hamiltonian* ham, const md_poles* po
         if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
     }
     return st2;
+}
+
+md_status md_density_matrix_rows(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,
+                                 const md_solver_opts* opts, double* rho_out, double* e_out,
+                                 double* rows_out, md_stats* stats, void* stream) {
+    clear_error();
+    md_status st = check_device();
+    if (st != MD_OK) return st;
+    if (!ham || !nodes) return set_error(MD_ERR_INVALID, "ham and nodes are required");
+    if (opts && opts->method == 1) return set_error(MD_ERR_INVALID, "density-matrix rows need method 0");
+    Regions R;
+    if ((st = make_regions(ham->h, nodes, R)) != MD_OK) return st;
+    const long long nn = (long long)R.desc.size();
+    if (nn > 0 && !rows_out) return set_error(MD_ERR_INVALID, "rows_out is NULL");
+    std::vector<long long> off(nn + 1, 0);
+    for (long long j = 0; j < nn; ++j) off[j + 1] = off[j] + R.points[j];
+    cudaStream_t s = (cudaStream_t)stream;
+    long long* d_off = nullptr;
+    auto cu = [&](cudaError_t e) -> md_status {
+        if (e == cudaSuccess) return MD_OK;
+        cudaFree(d_off);
+        return set_error(e == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA,
+                         std::string("CUDA: ") + cudaGetErrorString(e));
+    };
+    if (nn > 0) {
+        if ((st = cu(cudaMalloc(&d_off, (nn + 1) * sizeof(long long)))) != MD_OK) return st;
+        if ((st = cu(cudaMemcpyAsync(d_off, off.data(), (nn + 1) * sizeof(long long), cudaMemcpyHostToDevice, s))) !=
+            MD_OK)
+            return st;
+        if ((st = cu(cudaMemsetAsync(rows_out, 0, off[nn] * sizeof(double), s))) != MD_OK) return st;
+    }
+    md_solver_opts o = opts ? *opts : md_solver_opts{};
+    if (!opts) {
+        o.tol = 1e-10;
+        o.maxit = 20000;
+        o.precision = MD_PREC_MIXED;
+    }
+    if (o.kernel == 2) o.kernel = 1;   // the row epilogue lives in the generic kernel
+    FusedArgs fa{nullptr, nullptr, nullptr, rows_out, d_off};
+    md_plan* pl = nullptr;
+    st = plan_create(ham, poles, nodes, &o, rho_out, e_out, nullptr, true, s, &pl, &fa);
+    if (st != MD_OK) {
+        cudaFree(d_off);
+        return st;
+    }
+    md_status st2 = MD_OK;
+    if (pl->n_sys > 0) {
+        st = plan_launch(pl, s);
+        if (st == MD_OK) st2 = plan_stats(pl, s, stats);
+    } else if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+    }
+    plan_free(pl);
+    cudaStreamSynchronize(s);
+    cudaFree(d_off);
+    return st != MD_OK ? st : st2;
 }
 
 md_status md_plan_create(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,

@@ -133,8 +133,11 @@ __device__ __noinline__ void shifted_update(const SolveParams& P, Shared& S) {
                     }
                 }
 
-template <class Mode, int Q>
-__global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolveParams P) {
+// kMinB = 1: up to 1,024 threads, 64 registers; kMinB = 3: 512 threads and
+// 40 registers, so that three CTAs (three systems) share an SM; the loop is
+// latency-bound and the extra resident warps hide more of it.
+template <class Mode, int Q, int kMinB>
+__global__ void __launch_bounds__(kMinB == 1 ? 1024 : 512, kMinB) k_cocg(const __grid_constant__ SolveParams P) {
     using R = typename Mode::real;
     using C = typename Mode::cplx;
     __shared__ Shared S;
@@ -444,6 +447,15 @@ __global__ void __launch_bounds__(1024) k_cocg(const __grid_constant__ SolvePara
                 atomicAdd(P.fused_dLdV + gi, -(c_re * sq_im + c_im * sq_re));
             }
         }
+        if (P.dm_rows) {
+            // row j of the density matrix over the region: sum_p Im(w_p x_jp(k))
+            const double2 wp = P.w[sd.pole];
+            double* row = P.dm_rows + P.dm_off[sd.node];
+            for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
+                const double2 xv = x[i];
+                atomicAdd(row + i, wp.x * xv.y + wp.y * xv.x);
+            }
+        }
         if (P.multishift) {
             for (int k = threadIdx.x; k < P.P; k += blockDim.x) {
                 const long long o = (long long)sd.node * P.P + k;
@@ -617,7 +629,6 @@ __device__ __forceinline__ void zm_stencil_pass(const SolveParams& P, const Geo&
     float2* pbuf = reinterpret_cast<float2*>(dsm + L.plane_off);
     float* cacc = reinterpret_cast<float*>(dsm + L.cacc_off);
     unsigned char* stage = dsm + L.stage_off;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
     // staging offset (elements) of the plane start inside a 16-byte aligned copy
     const int soff = (int)((((uintptr_t)r) & 15) / 8);   // r and p share the residue per plane parity
     int col[K], sidx[K];
@@ -1016,17 +1027,17 @@ struct FP64Mode {
 };
 using MixedMode = MixedModeT;
 
-template <class Mode>
+template <class Mode, int kMinB>
 cudaError_t launch_q(const SolveParams& P, int grid, int block, cudaStream_t stream) {
     switch (P.q) {
-        case 1: k_cocg<Mode, 1><<<grid, block, 0, stream>>>(P); break;
-        case 2: k_cocg<Mode, 2><<<grid, block, 0, stream>>>(P); break;
-        case 3: k_cocg<Mode, 3><<<grid, block, 0, stream>>>(P); break;
-        case 4: k_cocg<Mode, 4><<<grid, block, 0, stream>>>(P); break;
-        case 5: k_cocg<Mode, 5><<<grid, block, 0, stream>>>(P); break;
-        case 6: k_cocg<Mode, 6><<<grid, block, 0, stream>>>(P); break;
-        case 7: k_cocg<Mode, 7><<<grid, block, 0, stream>>>(P); break;
-        case 8: k_cocg<Mode, 8><<<grid, block, 0, stream>>>(P); break;
+        case 1: k_cocg<Mode, 1, kMinB><<<grid, block, 0, stream>>>(P); break;
+        case 2: k_cocg<Mode, 2, kMinB><<<grid, block, 0, stream>>>(P); break;
+        case 3: k_cocg<Mode, 3, kMinB><<<grid, block, 0, stream>>>(P); break;
+        case 4: k_cocg<Mode, 4, kMinB><<<grid, block, 0, stream>>>(P); break;
+        case 5: k_cocg<Mode, 5, kMinB><<<grid, block, 0, stream>>>(P); break;
+        case 6: k_cocg<Mode, 6, kMinB><<<grid, block, 0, stream>>>(P); break;
+        case 7: k_cocg<Mode, 7, kMinB><<<grid, block, 0, stream>>>(P); break;
+        case 8: k_cocg<Mode, 8, kMinB><<<grid, block, 0, stream>>>(P); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -1112,9 +1123,13 @@ size_t slot_bytes_for(int precision, long long n_max) {
     return nm * (3 * sizeof(double2) + sizeof(double2));
 }
 
-cudaError_t launch_cocg(const SolveParams& P, int precision, int grid, int block, cudaStream_t stream) {
-    if (precision == MD_PREC_MIXED) return launch_q<MixedMode>(P, grid, block, stream);
-    return launch_q<FP64Mode>(P, grid, block, stream);
+cudaError_t launch_cocg(const SolveParams& P, int precision, int grid, int block, int per_sm,
+                        cudaStream_t stream) {
+    if (precision == MD_PREC_MIXED) {
+        if (per_sm >= 3 && block <= 512) return launch_q<MixedMode, 3>(P, grid, block, stream);
+        return launch_q<MixedMode, 1>(P, grid, block, stream);
+    }
+    return launch_q<FP64Mode, 1>(P, grid, block, stream);
 }
 
 cudaError_t launch_accumulate(int n_nodes, int Pn, const double2* x_src, const double2* z,

@@ -73,6 +73,10 @@ struct SolveParams {
     const double* fused_a;          // dL/drho per node, or NULL (= 0)
     const double* fused_b;          // dL/de per node, or NULL (= 0)
     const double2* w;               // pole weights
+    // density-matrix rows: when dm_rows != NULL every converged system adds
+    // Im(w_p x(k)) to dm_rows[dm_off[node] + k] (k region-local)
+    double* dm_rows;
+    const long long* dm_off;
     double2* ckpt;                  // NULL or checkpoint base
     const long long* ckpt_sys_off;  // point offset of system (node*P + pole) in ckpt
     unsigned int* work_counter;
@@ -92,7 +96,10 @@ int zm_max_threads(int K);
 size_t zm_smem_bytes(int q, int max_m0, int max_m1);
 int zm_occupancy(int q, int K, int block, size_t smem);   // resident CTAs per SM
 cudaError_t launch_cocg_zm(const SolveParams& P, int K, int grid, int block, size_t smem, cudaStream_t stream);
-cudaError_t launch_cocg(const SolveParams& P, int precision, int grid, int block, cudaStream_t stream);
+// per_sm >= 3 with block <= 512 (mixed precision) selects the instance
+// compiled for three resident CTAs per SM (40 registers per thread).
+cudaError_t launch_cocg(const SolveParams& P, int precision, int grid, int block, int per_sm,
+                        cudaStream_t stream);
 cudaError_t launch_accumulate(int n_nodes, int Pn, const double2* x_src, const double2* z,
                               const double2* w, double dV, double* rho, double* e, cudaStream_t stream);
 
