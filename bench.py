@@ -38,14 +38,16 @@ sys.path.insert(0, ROOT)
 METRIC = "(node,pole) solves/sec and density nodes/sec at rel err<=1e-6; matvec HBM GB/s"
 BYTES_PER_POINT_ITER = {"mixed": 80.0, "fp64": 160.0}
 # DRAM bytes (read + write) per region-point iteration of the solver kernel,
-# from one ncu capture (summary under profiles/, kernel k_cocg, bulk
-# workload, 19 nodes x 16 poles, 150-iteration cap), scaled to a full launch
-# by its region-point iterations.  Valid only for the kernel sources with the
+# from one ncu capture (summary under profiles/: kernel k_cocg, bulk
+# workload, 32 nodes x 16 poles, 150-iteration cap), keyed by precision and
+# launch shape (threads per CTA, CTAs per SM), scaled to a full launch by
+# its region-point iterations.  Valid only for the kernel sources with the
 # fingerprint below; any change to them makes the figure stale (null).
-TRAFFIC_PER_POINT_ITER = {"mixed": 71.25}
+TRAFFIC_PER_POINT_ITER = {("mixed", 512, 3): 114.2}
 TRAFFIC_SOURCES = ("paper_1907_02604_gb300/csrc/md_solver.cu", "paper_1907_02604_gb300/csrc/md_solver.h",
-                   "paper_1907_02604_gb300/csrc/md_device.cuh", "paper_1907_02604_gb300/csrc/md_internal.h")
-TRAFFIC_FINGERPRINT = "46e1e2f283a5251e:3cfa4a58ef899e74:6685de8068da134b:8141b58091ef73d1"
+                   "paper_1907_02604_gb300/csrc/md_device.cuh", "paper_1907_02604_gb300/csrc/md_internal.h",
+                   "paper_1907_02604_gb300/csrc/md_operator.cuh")
+TRAFFIC_FINGERPRINT = "dd555811318209dc:c156daa5b1c36f8f:6685de8068da134b:8141b58091ef73d1:0599288e211ef0fe"
 FLOPS_PER_POINT_ITER_8TH = 200.0
 
 
@@ -290,11 +292,14 @@ def main():
     conv = sum(s["n_converged"] for s in stats)
     B = BYTES_PER_POINT_ITER[prec]
     achieved = point_iters * B / (kernel_ms / 1e3) / 1e9
-    traffic = None
-    if prec in TRAFFIC_PER_POINT_ITER and kernel_fingerprint() == TRAFFIC_FINGERPRINT:
-        traffic = TRAFFIC_PER_POINT_ITER[prec] * point_iters / len(stats)   # bytes per launch
-    peak, peak_kind = read_peaks()
     shape = plans[0].launch_shape()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    per_sm = shape[1] // n_sm if shape[1] % n_sm == 0 else 0
+    tkey = (prec, shape[0], per_sm)
+    traffic = None
+    if tkey in TRAFFIC_PER_POINT_ITER and kernel_fingerprint() == TRAFFIC_FINGERPRINT:
+        traffic = TRAFFIC_PER_POINT_ITER[tkey] * point_iters / len(stats)   # bytes per launch
+    peak, peak_kind = read_peaks()
 
     from dataclasses import replace as _replace
 
