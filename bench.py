@@ -47,7 +47,7 @@ TRAFFIC_PER_POINT_ITER = {("mixed", 512, 3): 114.2}
 TRAFFIC_SOURCES = ("paper_1907_02604_gb300/csrc/md_solver.cu", "paper_1907_02604_gb300/csrc/md_solver.h",
                    "paper_1907_02604_gb300/csrc/md_device.cuh", "paper_1907_02604_gb300/csrc/md_internal.h",
                    "paper_1907_02604_gb300/csrc/md_operator.cuh")
-TRAFFIC_FINGERPRINT = "dd555811318209dc:c156daa5b1c36f8f:6685de8068da134b:8141b58091ef73d1:0599288e211ef0fe"
+TRAFFIC_FINGERPRINT = "dd555811318209dc:c156daa5b1c36f8f:6685de8068da134b:8141b58091ef73d1:c7ead1179eba392c"
 FLOPS_PER_POINT_ITER_8TH = 200.0
 
 
@@ -345,31 +345,45 @@ def main():
         fp64_form["speedup_mixed_over_fp64"] = value / fp64_form["value"]
 
     # ---- side measurement: the paper's Lanczos quadrature (Eq. 9, K = 40) --
+    # in FP64 and with FP32 vectors; the mixed densities are compared with
+    # the FP64 ones on the same batches
     lssgq = None
     if not args.no_lssgq:
         from paper_1907_02604_gb300 import lssgq_rules
         K = 40
 
-        def lssgq_step(i):
-            nd, hw = batch(i)
-            R = lssgq_rules(ham, nd, hw, K=K, stream=stream)
-            R.fields(w.mu, w.kT, stream=stream)
-            return R
+        def lssgq_run(precision):
+            def step(i):
+                nd, hw = batch(i)
+                R = lssgq_rules(ham, nd, hw, K=K, precision=precision, stream=stream)
+                rho, _, _ = R.fields(w.mu, w.kT, stream=stream)
+                return R, rho
 
-        for i in range(args.warmup):
-            lssgq_step(i)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rules = [lssgq_step(args.warmup + i) for i in range(args.steps)]
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
+            for i in range(args.warmup):
+                step(i)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = [step(args.warmup + i) for i in range(args.steps)]
+            torch.cuda.synchronize()
+            return out, time.perf_counter() - t0
+
         pts = sum(int(np.sum((2 * batch(args.warmup + i)[1].astype(np.int64) + 1) ** 3)) for i in range(args.steps))
-        steps_taken = sum(int(R.k_used.sum()) for R in rules)
-        lssgq = {"value": sum(R.n_nodes for R in rules) * world / el, "unit": "density nodes/s",
-                 "K": K, "ms_per_step": 1e3 * el / args.steps,
-                 "point_iters_per_s": pts * K * world / el, "lanczos_steps": steps_taken,
-                 "note": "Lanczos Gauss rules (FP64) + fields at (mu, kT); host-timed, includes the "
-                         "per-call work-list upload and status read-back"}
+        lssgq = {}
+        ref = None
+        for precision in ("fp64", "mixed"):
+            out, el = lssgq_run(precision)
+            entry = {"value": sum(R.n_nodes for R, _ in out) * world / el, "unit": "density nodes/s",
+                     "K": K, "ms_per_step": 1e3 * el / args.steps,
+                     "point_iters_per_s": pts * K * world / el,
+                     "lanczos_steps": sum(int(R.k_used.sum()) for R, _ in out)}
+            if ref is None:
+                ref = [rho for _, rho in out]
+            else:
+                entry["max_rel_diff_rho_vs_fp64"] = max(float((rho - r).abs().max() / r.abs().max())
+                                                        for (_, rho), r in zip(out, ref))
+            lssgq[precision] = entry
+        lssgq["note"] = ("Lanczos Gauss rules + fields at (mu, kT); host-timed, includes the per-call "
+                         "work-list upload and status read-back")
 
     # ---- end to end through the C ABI from host buffers -------------------
     e2e = None

@@ -357,6 +357,10 @@ typedef struct {
                               the Krylov space being invariant (0 = 1e-13) */
     double timeout_s;      /* device wall-clock budget, 0 = none */
     int32_t block;         /* threads per CTA, 0 = 512; multiple of 32 in 64..1024 */
+    int32_t precision;     /* MD_PREC_FP64: FP64 Lanczos vectors and arithmetic;
+                              MD_PREC_MIXED: FP32 vectors, stencil and projector
+                              terms with compensated FP32 partial sums, FP64
+                              reductions, alpha, beta and vector scales */
 } md_lssgq_opts;
 
 /* Gauss rules of every node: lambda_out, weight_out (device, n_nodes x K

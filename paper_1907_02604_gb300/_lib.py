@@ -55,7 +55,7 @@ class md_solver_opts(ctypes.Structure):
 
 class md_lssgq_opts(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("breakdown_tol", ctypes.c_double), ("timeout_s", ctypes.c_double),
-                ("block", ctypes.c_int32)]
+                ("block", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 class md_stats(ctypes.Structure):

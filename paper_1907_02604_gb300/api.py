@@ -418,13 +418,15 @@ class GaussRules:
 
 
 def lssgq_rules(ham: Hamiltonian, nodes, halfwidth, K: int = 40, breakdown_tol: float = 0.0,
-                timeout_s: float = 0.0, block: int = 0, stream=None) -> GaussRules:
-    """K-point Lanczos Gauss rules of every node (Section 2.1, Eq. 9)."""
+                timeout_s: float = 0.0, block: int = 0, precision: str = "fp64", stream=None) -> GaussRules:
+    """K-point Lanczos Gauss rules of every node (Section 2.1, Eq. 9);
+    precision "fp64" or "mixed" (FP32 vectors, FP64 scalars)."""
     na = _NodeArgs(nodes, halfwidth)
     lam = torch.empty((na.n, K), dtype=torch.float64, device="cuda")
     wt = torch.empty((na.n, K), dtype=torch.float64, device="cuda")
     ku = torch.empty(na.n, dtype=torch.int32, device="cuda")
-    o = _lib.md_lssgq_opts(int(K), float(breakdown_tol), float(timeout_s), int(block))
+    prec = {"fp64": _lib.MD_PREC_FP64, "mixed": _lib.MD_PREC_MIXED}[precision]
+    o = _lib.md_lssgq_opts(int(K), float(breakdown_tol), float(timeout_s), int(block), prec)
     check(load().md_lssgq_rules(ham.handle, ctypes.byref(na.c), ctypes.byref(o), ctypes.c_void_p(lam.data_ptr()),
                                 ctypes.c_void_p(wt.data_ptr()), ctypes.c_void_p(ku.data_ptr()),
                                 _stream_handle(stream)), "md_lssgq_rules")

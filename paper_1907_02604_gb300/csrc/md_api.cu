@@ -999,6 +999,8 @@ extern "C" md_status md_lssgq_rules(const md_hamiltonian* ham, const md_nodes* n
         return set_error(MD_ERR_INVALID, "opts: breakdown_tol and timeout_s must be >= 0");
     if (opts->block != 0 && (opts->block < 64 || opts->block > 1024 || opts->block % 32))
         return set_error(MD_ERR_INVALID, "opts.block must be 0 or a multiple of 32 in 64..1024");
+    if (opts->precision != MD_PREC_FP64 && opts->precision != MD_PREC_MIXED)
+        return set_error(MD_ERR_INVALID, "opts.precision must be MD_PREC_FP64 or MD_PREC_MIXED");
     Ham& H = const_cast<md_hamiltonian*>(ham)->h;
     Regions R;
     if ((st = make_regions(H, nodes, R)) != MD_OK) return st;
@@ -1025,7 +1027,8 @@ extern "C" md_status md_lssgq_rules(const md_hamiltonian* ham, const md_nodes* n
     P.n_sys = (int)nn;
     P.timeout_ns = opts->timeout_s > 0 ? (unsigned long long)(opts->timeout_s * 1e9) : 0ULL;
     P.n_max = (int)((R.n_max + 63) / 64 * 64);
-    P.slot_bytes = ((size_t)2 * P.n_max * sizeof(double) + 511) / 512 * 512;
+    const size_t elem = opts->precision == MD_PREC_MIXED ? sizeof(float) : sizeof(double);
+    P.slot_bytes = ((size_t)2 * P.n_max * elem + 511) / 512 * 512;
 
     SysDesc* d_sys = nullptr;
     NodeDesc* d_nodes = nullptr;
@@ -1081,7 +1084,7 @@ extern "C" md_status md_lssgq_rules(const md_hamiltonian* ham, const md_nodes* n
     L.beta = d_beta;
     L.k_used = d_kused;
     L.status = d_status;
-    LTRY(launch_lanczos(P, L, grid, block, s));
+    LTRY(launch_lanczos(P, L, opts->precision, grid, block, s));
     LTRY(launch_gauss_rules((int)nn, L, lambda_out, weight_out, s));
     if (k_used_out)
         LTRY(cudaMemcpyAsync(k_used_out, d_kused, nn * sizeof(int), cudaMemcpyDeviceToDevice, s));

@@ -3,7 +3,8 @@
 //
 // k_lanczos: one CTA per node at a time (persistent, cost-sorted work list),
 //   K steps of the symmetric Lanczos process on H_R(j) from q_1 = e_j in
-//   FP64 real arithmetic, no reorthogonalisation.  Two region vectors per
+//   real arithmetic (FP64, or FP32 vectors with FP64 scalars), no
+//   reorthogonalisation.  Two region vectors per
 //   CTA, each kept with a scale (q = sigma u) so that normalising the new
 //   Lanczos vector costs no pass of its own.  Per step:
 //     NL  c_al = sum_i p_al(i) u_c(i)                 (nonlocal coefficients)
@@ -30,6 +31,7 @@
 
 #include <cfloat>
 #include <cstdint>
+#include <type_traits>
 
 #include "md_lanczos.h"
 #include "md_operator.cuh"
@@ -38,14 +40,32 @@ namespace md {
 
 namespace {
 
-template <int Q>
+// Block-wide sums of float-float partials, broadcast to every thread.
+template <int K>
+__device__ __forceinline__ void block_sum_ff(Shared& S, const float (&hi)[K], const float (&lo)[K],
+                                             double (&v)[K]) {
+    block_reduce_ff<K>(S, hi, lo, v);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < K; ++k) S.bcast[k] = v[k];
+    __syncthreads();
+    for (int k = 0; k < K; ++k) v[k] = S.bcast[k];
+}
+
+// R = double: FP64 vectors and arithmetic.  R = float: FP32 vectors,
+// stencil and projector terms, compensated FP32 partial sums reduced in
+// float-float and FP64; alpha, beta and the vector scales stay FP64.
+template <class R, int Q>
 __global__ void __launch_bounds__(1024) k_lanczos(const __grid_constant__ SolveParams P,
                                                   const LanczosParams L) {
     __shared__ Shared S;
+    constexpr bool kF32 = std::is_same<R, float>::value;
     const uint64_t t_start = global_time_ns();
-    double* const u0 = reinterpret_cast<double*>(P.scratch + (size_t)blockIdx.x * P.slot_bytes);
-    double* const u1 = u0 + P.n_max;
-    for (int t = threadIdx.x; t < 3 * kMaxQ; t += blockDim.x) (&S.coefD[0][0])[t] = (&P.coef[0][0])[t];
+    R* const u0 = reinterpret_cast<R*>(P.scratch + (size_t)blockIdx.x * P.slot_bytes);
+    R* const u1 = u0 + P.n_max;
+    for (int t = threadIdx.x; t < 3 * kMaxQ; t += blockDim.x) {
+        (&S.coefD[0][0])[t] = (&P.coef[0][0])[t];
+        (&S.coefF[0][0])[t] = (float)(&P.coef[0][0])[t];
+    }
     if (P.nonlocal && P.n_atoms <= kMapMax)
         for (int t = threadIdx.x; t < P.n_atoms; t += blockDim.x) S.map[t] = -1;
 
@@ -75,11 +95,11 @@ __global__ void __launch_bounds__(1024) k_lanczos(const __grid_constant__ SolveP
         const long long base = (long long)node * L.K;
 
         if (P.nonlocal) collect_local_atoms(P, G, S);
-        double* uc = u0;
-        double* up = u1;
+        R* uc = u0;
+        R* up = u1;
         for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
-            uc[i] = (i == G.src) ? 1.0 : 0.0;
-            up[i] = 0.0;
+            uc[i] = (i == G.src) ? (R)1 : (R)0;
+            up[i] = (R)0;
         }
         double sc = 1.0, sp = 0.0, bprev = 0.0, scale = 0.0;
         int k_done = 0;
@@ -93,32 +113,59 @@ __global__ void __launch_bounds__(1024) k_lanczos(const __grid_constant__ SolveP
                 timed_out = true;
                 break;
             }
-            if (P.nonlocal) nonlocal_coeffs<double, double>(P, G, S, uc);
-            double acc[1] = {0.0};
+            if (P.nonlocal) nonlocal_coeffs<R, R>(P, G, S, uc);
             const double cb = bprev * sp;
-            for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
-                const double y = matvec_point<double, double, Q, double>(P, G, S, uc, i, 0.0, 0.0, P.diag);
-                const double wv = sc * y - cb * up[i];
-                up[i] = wv;
-                acc[0] += uc[i] * wv;
+            double a, b;
+            if constexpr (kF32) {
+                const float scf = (float)sc, cbf = (float)cb;
+                KSum<float> acc;
+                for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
+                    const float y = matvec_point<float, float, Q, float>(P, G, S, uc, i, 0.f, 0.f, (float)P.diag);
+                    const float wv = scf * y - cbf * up[i];
+                    up[i] = wv;
+                    acc.add(uc[i] * wv);
+                }
+                double t1[1];
+                const float h1[1] = {acc.hi()}, l1[1] = {acc.lo()};
+                block_sum_ff<1>(S, h1, l1, t1);
+                a = sc * t1[0];
+                const float caf = (float)(a * sc);
+                KSum<float> acc2;
+                for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
+                    const float wv = up[i] - caf * uc[i];
+                    up[i] = wv;
+                    acc2.add(wv * wv);
+                }
+                double t2[1];
+                const float h2[1] = {acc2.hi()}, l2[1] = {acc2.lo()};
+                block_sum_ff<1>(S, h2, l2, t2);
+                b = sqrt(t2[0]);
+            } else {
+                double acc[1] = {0.0};
+                for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
+                    const double y = matvec_point<double, double, Q, double>(P, G, S, uc, i, 0.0, 0.0, P.diag);
+                    const double wv = sc * y - cb * up[i];
+                    up[i] = wv;
+                    acc[0] += uc[i] * wv;
+                }
+                block_sum<1>(S, acc);
+                a = sc * acc[0];
+                const double ca = a * sc;
+                double acc2[1] = {0.0};
+                for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
+                    const double wv = up[i] - ca * uc[i];
+                    up[i] = wv;
+                    acc2[0] += wv * wv;
+                }
+                block_sum<1>(S, acc2);
+                b = sqrt(acc2[0]);
             }
-            block_sum<1>(S, acc);
-            const double a = sc * acc[0];
-            const double ca = a * sc;
-            double acc2[1] = {0.0};
-            for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
-                const double wv = up[i] - ca * uc[i];
-                up[i] = wv;
-                acc2[0] += wv * wv;
-            }
-            block_sum<1>(S, acc2);
-            const double b = sqrt(acc2[0]);
             if (k == 0) scale = fabs(a) + b + 1.0;
             if (threadIdx.x == 0) L.alpha[base + k] = a;
             k_done = k + 1;
             if (k == L.K - 1 || b <= L.breakdown_tol * scale) break;
             if (threadIdx.x == 0) L.beta[base + k] = b;
-            double* t = uc;
+            R* t = uc;
             uc = up;
             up = t;
             sp = sc;
@@ -323,22 +370,29 @@ __global__ void __launch_bounds__(1024) k_fermi_level(int n_nodes, int K, const 
     }
 }
 
-}  // namespace
-
-cudaError_t launch_lanczos(const SolveParams& P, const LanczosParams& L, int grid, int block,
-                           cudaStream_t stream) {
+template <class R>
+cudaError_t launch_lanczos_r(const SolveParams& P, const LanczosParams& L, int grid, int block,
+                             cudaStream_t stream) {
     switch (P.q) {
-        case 1: k_lanczos<1><<<grid, block, 0, stream>>>(P, L); break;
-        case 2: k_lanczos<2><<<grid, block, 0, stream>>>(P, L); break;
-        case 3: k_lanczos<3><<<grid, block, 0, stream>>>(P, L); break;
-        case 4: k_lanczos<4><<<grid, block, 0, stream>>>(P, L); break;
-        case 5: k_lanczos<5><<<grid, block, 0, stream>>>(P, L); break;
-        case 6: k_lanczos<6><<<grid, block, 0, stream>>>(P, L); break;
-        case 7: k_lanczos<7><<<grid, block, 0, stream>>>(P, L); break;
-        case 8: k_lanczos<8><<<grid, block, 0, stream>>>(P, L); break;
+        case 1: k_lanczos<R, 1><<<grid, block, 0, stream>>>(P, L); break;
+        case 2: k_lanczos<R, 2><<<grid, block, 0, stream>>>(P, L); break;
+        case 3: k_lanczos<R, 3><<<grid, block, 0, stream>>>(P, L); break;
+        case 4: k_lanczos<R, 4><<<grid, block, 0, stream>>>(P, L); break;
+        case 5: k_lanczos<R, 5><<<grid, block, 0, stream>>>(P, L); break;
+        case 6: k_lanczos<R, 6><<<grid, block, 0, stream>>>(P, L); break;
+        case 7: k_lanczos<R, 7><<<grid, block, 0, stream>>>(P, L); break;
+        case 8: k_lanczos<R, 8><<<grid, block, 0, stream>>>(P, L); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_lanczos(const SolveParams& P, const LanczosParams& L, int precision, int grid, int block,
+                           cudaStream_t stream) {
+    if (precision == MD_PREC_MIXED) return launch_lanczos_r<float>(P, L, grid, block, stream);
+    return launch_lanczos_r<double>(P, L, grid, block, stream);
 }
 
 cudaError_t launch_gauss_rules(int n_nodes, const LanczosParams& L, double* lambda, double* weight,

@@ -21,8 +21,10 @@ struct LanczosParams {
 };
 
 // Lanczos on every node of P.sys (pole fields unused); P.scratch holds one
-// slot of 2 n_max doubles per CTA.
-cudaError_t launch_lanczos(const SolveParams& P, const LanczosParams& L, int grid, int block,
+// slot per CTA.
+// precision: MD_PREC_FP64 (FP64 vectors) or MD_PREC_MIXED (FP32 vectors and
+// stencil, FP64 scalars); slot = 2 n_max values of that width.
+cudaError_t launch_lanczos(const SolveParams& P, const LanczosParams& L, int precision, int grid, int block,
                            cudaStream_t stream);
 // Nodes and weights of each node's Gauss rule (ascending nodes; positions
 // past k_used get the largest node and weight 0).

@@ -99,6 +99,10 @@ template <class R>
 __device__ __forceinline__ R re_of(double v) { return (R)v; }
 template <class R>
 __device__ __forceinline__ R im_of(double) { return (R)0; }
+template <class R>
+__device__ __forceinline__ R re_of(float v) { return (R)v; }
+template <class R>
+__device__ __forceinline__ R im_of(float) { return (R)0; }
 template <class C>
 struct VMake {
     template <class R>
@@ -108,6 +112,11 @@ template <>
 struct VMake<double> {
     template <class R>
     __device__ static double make(R re, R) { return (double)re; }
+};
+template <>
+struct VMake<float> {
+    template <class R>
+    __device__ static float make(R re, R) { return (float)re; }
 };
 
 struct Geo {

@@ -174,3 +174,16 @@ def test_invalid_inputs_raise(bad):
     with pytest.raises(MacroDFTError) as ei:
         density(ham, z, wt, nodes, hw, opts)
     assert ei.value.status == MD_ERR_INVALID
+
+
+@pytest.mark.parametrize("n_poles", [2, 64])
+def test_fewest_and_most_poles(n_poles):
+    """P = 2 (one trapezoid node) and P = 64 (the shifted-COCG maximum), per
+    pole and shifted, against the oracle."""
+    w = make_workload("tiny", shape=(9, 10, 11), fd_order=4, s=2, n_nodes=4, n_poles=n_poles)
+    w.tol = 1e-11
+    _, o = oracle_run(w)
+    for method in ("cocg", "shifted"):
+        g = gpu_run(w, precision="fp64", method=method)
+        assert rel_err(g["rho"], o.rho) <= FP64_BAR, method
+        assert rel_err(g["e"], o.e_node) <= FP64_BAR, method
