@@ -332,14 +332,19 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
     const long long nw = pl->P.n_sys;   // work items (systems, or nodes with shifted COCG)
     int max_per = 1;
     for (const auto& c : cands) max_per = std::max(max_per, c.per_sm);
-    // enough systems that every candidate's CTAs each take two in turn
-    const long long ns = std::min<long long>(nw, 2LL * n_sm * max_per);
+    // enough systems that every candidate's CTAs each take four in turn, so
+    // that the trial's tail (CTAs idle at its end) weighs little, as in a
+    // full batch
+    const long long ns = std::min<long long>(nw, 4LL * n_sm * max_per);
     std::vector<SysDesc> all(nw), sample;
     PLAN_TRY(cudaMemcpy(all.data(), pl->d_sys, nw * sizeof(SysDesc), cudaMemcpyDeviceToHost));
     for (long long k = 0; k < ns; ++k) sample.push_back(all[(k * nw) / ns]);
     SysDesc* d_sample = nullptr;
     PLAN_TRY(cudaMalloc(&d_sample, ns * sizeof(SysDesc)));
     cudaMemcpy(d_sample, sample.data(), ns * sizeof(SysDesc), cudaMemcpyHostToDevice);
+    // iterations per trial system (MD_AUTOTUNE_ITERS overrides, 16..4096)
+    int trial_iters = 64;
+    if (const char* ev = std::getenv("MD_AUTOTUNE_ITERS")) trial_iters = std::max(16, std::min(4096, std::atoi(ev)));
     double best = -1.0;
     Shape bs = cands[0];
     std::vector<int> h_it(pl->n_sys);
@@ -351,7 +356,7 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
         SolveParams T = pl->P;
         T.sys = d_sample;
         T.n_sys = (int)ns;
-        T.maxit = std::min(pl->P.maxit, 64);
+        T.maxit = std::min(pl->P.maxit, trial_iters);
         T.ckpt = nullptr;         // trials never touch the checkpoint
         T.fused_dLdV = nullptr;   // nor the gradient
         T.dm_rows = nullptr;
