@@ -441,7 +441,8 @@ def main():
         "dtype": "f32+f64" if prec == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": w.name, "nodes_per_step": bs, "poles": w.n_poles,
-                   "region": "33^3", "grid": list(w.shape), "atoms": len(w.atoms),
+                   "region": (f"{2 * int(w.halfwidth.min()) + 1}^3" if w.halfwidth.min() == w.halfwidth.max() else
+                              f"{2 * int(w.halfwidth.min()) + 1}^3..{2 * int(w.halfwidth.max()) + 1}^3"), "grid": list(w.shape), "atoms": len(w.atoms),
                    "fd_order": w.fd_order, "precision": prec, "tol": w.tol,
                    "l2": "no flush: per-step working set (Krylov slots) > 129 MB L2",
                    "parallelism": f"nodes sharded over {world} GPU(s), no collective"},
