@@ -39,11 +39,12 @@ METRIC = "(node,pole) solves/sec and density nodes/sec at rel err<=1e-6; matvec 
 BYTES_PER_POINT_ITER = {"mixed": 80.0, "fp64": 160.0}
 # DRAM bytes (read + write) per region-point iteration of the solver kernel,
 # from one ncu capture (summary under profiles/: kernel k_cocg, bulk
-# workload, 32 nodes x 16 poles, 150-iteration cap), keyed by precision and
-# launch shape (threads per CTA, CTAs per SM), scaled to a full launch by
-# its region-point iterations.  Valid only for the kernel sources with the
-# fingerprint below; any change to them makes the figure stale (null).
-TRAFFIC_PER_POINT_ITER = {("mixed", 512, 3): 114.2}
+# workload, 32 nodes x 16 poles, 150-iteration cap), keyed by workload,
+# precision and launch shape (threads per CTA, CTAs per SM), scaled to a
+# full launch by its region-point iterations.  Valid only for the kernel
+# sources with the fingerprint below; any change to them makes the figure
+# stale (null).
+TRAFFIC_PER_POINT_ITER = {("bulk_mixed", "mixed", 512, 3): 114.2}
 TRAFFIC_SOURCES = ("paper_1907_02604_gb300/csrc/md_solver.cu", "paper_1907_02604_gb300/csrc/md_solver.h",
                    "paper_1907_02604_gb300/csrc/md_device.cuh", "paper_1907_02604_gb300/csrc/md_internal.h",
                    "paper_1907_02604_gb300/csrc/md_operator.cuh")
@@ -295,7 +296,7 @@ def main():
     shape = plans[0].launch_shape()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     per_sm = shape[1] // n_sm if shape[1] % n_sm == 0 else 0
-    tkey = (prec, shape[0], per_sm)
+    tkey = (w.name, prec, shape[0], per_sm)
     traffic = None
     if tkey in TRAFFIC_PER_POINT_ITER and kernel_fingerprint() == TRAFFIC_FINGERPRINT:
         traffic = TRAFFIC_PER_POINT_ITER[tkey] * point_iters / len(stats)   # bytes per launch
