@@ -48,7 +48,7 @@ TRAFFIC_PER_POINT_ITER = {("bulk_mixed", "mixed", 512, 3): 114.2}
 TRAFFIC_SOURCES = ("paper_1907_02604_gb300/csrc/md_solver.cu", "paper_1907_02604_gb300/csrc/md_solver.h",
                    "paper_1907_02604_gb300/csrc/md_device.cuh", "paper_1907_02604_gb300/csrc/md_internal.h",
                    "paper_1907_02604_gb300/csrc/md_operator.cuh")
-TRAFFIC_FINGERPRINT = "dd555811318209dc:c156daa5b1c36f8f:6685de8068da134b:8141b58091ef73d1:c7ead1179eba392c"
+TRAFFIC_FINGERPRINT = "dd555811318209dc:c156daa5b1c36f8f:6685de8068da134b:0fb5570fc87854c8:c7ead1179eba392c"
 FLOPS_PER_POINT_ITER_8TH = 200.0
 
 

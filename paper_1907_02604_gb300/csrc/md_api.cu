@@ -102,7 +102,7 @@ void free_ham(Ham& H) {
     void* ptrs[] = {H.V, H.V32, H.atom_xyz, H.atom_depth, H.atom_sigma, H.proj_i0, H.proj_len,
                     H.proj_d, H.proj_g, H.proj_d32, H.proj_g32, H.proj_C, H.proj_absum,
                     H.proj_C32, H.proj_rows, H.pl_ptr, H.pl_atom, H.pl_val32, H.pl_val64,
-                    H.scratch};
+                    H.scratch, H.lz_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1035,29 +1035,15 @@ extern "C" md_status md_lssgq_rules(const md_hamiltonian* ham, const md_nodes* n
     const size_t elem = opts->precision == MD_PREC_MIXED ? sizeof(float) : sizeof(double);
     P.slot_bytes = ((size_t)2 * P.n_max * elem + 511) / 512 * 512;
 
-    SysDesc* d_sys = nullptr;
-    NodeDesc* d_nodes = nullptr;
-    double *d_alpha = nullptr, *d_beta = nullptr;
-    int *d_kused = nullptr, *d_status = nullptr;
-    unsigned int* d_counter = nullptr;
-    auto release = [&]() {
-        cudaFree(d_sys);
-        cudaFree(d_nodes);
-        cudaFree(d_alpha);
-        cudaFree(d_beta);
-        cudaFree(d_kused);
-        cudaFree(d_status);
-        cudaFree(d_counter);
-    };
 #define LTRY(expr)                                                                                   \
     do {                                                                                             \
         cudaError_t _e = (expr);                                                                     \
-        if (_e != cudaSuccess) {                                                                     \
-            release();                                                                               \
+        if (_e != cudaSuccess)                                                                       \
             return set_error((_e == cudaErrorMemoryAllocation) ? MD_ERR_OOM : MD_ERR_CUDA,           \
                              std::string("CUDA: ") + cudaGetErrorString(_e) + " (" #expr ")");       \
-        }                                                                                            \
     } while (0)
+    // every call ends synchronised with its stream, so the cached buffers
+    // are idle whenever a call grows them
     const size_t need = P.slot_bytes * (size_t)grid;
     if (need > H.scratch_bytes) {
         LTRY(cudaStreamSynchronize(s));
@@ -1068,13 +1054,30 @@ extern "C" md_status md_lssgq_rules(const md_hamiltonian* ham, const md_nodes* n
         H.scratch_bytes = need;
     }
     P.scratch = (char*)H.scratch;
-    LTRY(cudaMalloc(&d_sys, nn * sizeof(SysDesc)));
-    LTRY(cudaMalloc(&d_nodes, nn * sizeof(NodeDesc)));
-    LTRY(cudaMalloc(&d_alpha, nn * K * sizeof(double)));
-    LTRY(cudaMalloc(&d_beta, nn * K * sizeof(double)));
-    LTRY(cudaMalloc(&d_kused, nn * sizeof(int)));
-    LTRY(cudaMalloc(&d_status, nn * sizeof(int)));
-    LTRY(cudaMalloc(&d_counter, sizeof(unsigned int)));
+    auto up256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t o_nodes = up256(nn * sizeof(SysDesc));
+    const size_t o_alpha = o_nodes + up256(nn * sizeof(NodeDesc));
+    const size_t o_beta = o_alpha + up256((size_t)nn * K * sizeof(double));
+    const size_t o_kused = o_beta + up256((size_t)nn * K * sizeof(double));
+    const size_t o_status = o_kused + up256(nn * sizeof(int));
+    const size_t o_counter = o_status + up256(nn * sizeof(int));
+    const size_t lz_need = o_counter + 256;
+    if (lz_need > H.lz_bytes) {
+        LTRY(cudaStreamSynchronize(s));
+        if (H.lz_buf) cudaFree(H.lz_buf);
+        H.lz_buf = nullptr;
+        H.lz_bytes = 0;
+        LTRY(cudaMalloc(&H.lz_buf, lz_need));
+        H.lz_bytes = lz_need;
+    }
+    char* lz = (char*)H.lz_buf;
+    SysDesc* d_sys = (SysDesc*)lz;
+    NodeDesc* d_nodes = (NodeDesc*)(lz + o_nodes);
+    double* d_alpha = (double*)(lz + o_alpha);
+    double* d_beta = (double*)(lz + o_beta);
+    int* d_kused = (int*)(lz + o_kused);
+    int* d_status = (int*)(lz + o_status);
+    unsigned int* d_counter = (unsigned int*)(lz + o_counter);
     LTRY(cudaMemcpyAsync(d_sys, sys.data(), nn * sizeof(SysDesc), cudaMemcpyHostToDevice, s));
     LTRY(cudaMemcpyAsync(d_nodes, R.desc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, s));
     LTRY(cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), s));
@@ -1097,7 +1100,6 @@ extern "C" md_status md_lssgq_rules(const md_hamiltonian* ham, const md_nodes* n
     LTRY(cudaMemcpyAsync(h_status.data(), d_status, nn * sizeof(int), cudaMemcpyDeviceToHost, s));
     LTRY(cudaStreamSynchronize(s));
 #undef LTRY
-    release();
     int worst = 0;
     for (int v : h_status) worst = (v == 4 || worst == 4) ? 4 : std::max(worst, v);
     if (worst == 4) return set_error(MD_ERR_TIMEOUT, "device time budget exhausted; rules incomplete");

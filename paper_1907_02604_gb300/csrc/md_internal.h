@@ -72,6 +72,9 @@ struct Ham {
     // cached solver scratch (grow-only)
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    // cached work lists and per-node Lanczos results of md_lssgq_rules (grow-only)
+    void* lz_buf = nullptr;
+    size_t lz_bytes = 0;
 };
 
 }  // namespace md
