@@ -362,9 +362,11 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
         T.dm_rows = nullptr;
         const int grid = (int)std::min<long long>((long long)n_sm * c.per_sm, ns);
         if (pl->P.slot_bytes * (size_t)grid > scratch_bytes) continue;
-        // best of two runs; the counter reset is ordered on the trial stream
+        // best of two runs (one for a z-march shape already far behind); the
+        // counter reset is ordered on the trial stream
         float ms = 0.f;
         bool failed = false;
+        long long pit = 0;
         for (int rep = 0; rep < 2 && !failed; ++rep) {
             cudaMemsetAsync(T.work_counter, 0, sizeof(unsigned int), pl->cap);
             cudaEventRecord(pl->ev0, pl->cap);
@@ -382,16 +384,18 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
             float t = 0.f;
             cudaEventElapsedTime(&t, pl->ev0, pl->ev1);
             if (rep == 0 || t < ms) ms = t;
+            if (rep == 0) {   // iteration counts are the same in every repetition
+                cudaMemcpy(h_it.data(), T.iters, pl->n_sys * sizeof(int), cudaMemcpyDeviceToHost);
+                for (const auto& sd : sample) {
+                    int it = h_it[(long long)sd.node * pl->Pn + sd.pole];
+                    if (pl->multishift)
+                        for (int p = 0; p < pl->Pn; ++p) it = std::max(it, h_it[(long long)sd.node * pl->Pn + p]);
+                    pit += (long long)it * pl->points[sd.node];
+                }
+                if (c.variant > 0 && ms > 0 && (double)pit / ms < 0.5 * best) break;
+            }
         }
         if (failed) continue;
-        cudaMemcpy(h_it.data(), T.iters, pl->n_sys * sizeof(int), cudaMemcpyDeviceToHost);
-        long long pit = 0;
-        for (const auto& sd : sample) {
-            int it = h_it[(long long)sd.node * pl->Pn + sd.pole];
-            if (pl->multishift)
-                for (int p = 0; p < pl->Pn; ++p) it = std::max(it, h_it[(long long)sd.node * pl->Pn + p]);
-            pit += (long long)it * pl->points[sd.node];
-        }
         const double rate = ms > 0 ? (double)pit / ms : 0.0;
         if (std::getenv("MD_AUTOTUNE_LOG"))
             std::fprintf(stderr, "md autotune: variant %d block %d ctas/SM %d: %.3f ms, %.3g point-iterations/s\n",

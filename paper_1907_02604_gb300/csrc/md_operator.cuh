@@ -414,6 +414,8 @@ __device__ void nonlocal_coeffs(const SolveParams& P, const Geo& G, Shared& S, c
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
                 const int lo = max(u0, rx.lo[t]), hi = min(u1, rx.hi[t]);
+                // unrolled so that a lane has several of its row's loads in flight
+#pragma unroll 4
                 for (int u = lo; u <= hi; ++u) {
                     const C pv = vrow[u + rx.shift[t]];
                     const R g1 = __ldg(gx + u);
