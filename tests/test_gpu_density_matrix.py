@@ -42,3 +42,18 @@ def test_rows_symmetric_on_whole_cell():
     for a in range(3):
         for b in range(3):
             assert abs(rows[a][g[b]] - rows[b][g[a]]) <= 1e-9 * np.abs(rows[a]).max()
+
+
+def test_rows_refuse_shifted_and_accept_empty():
+    """The rows need every pole's own solution vector, which shifted COCG
+    does not keep; an empty node list returns empty outputs."""
+    from paper_1907_02604_gb300 import Hamiltonian, SolverOptions, density_matrix_rows, make_poles
+    from paper_1907_02604_gb300._lib import MacroDFTError, MD_ERR_INVALID
+    w = make_workload("tiny")
+    ham = Hamiltonian.from_workload(w)
+    z, wt = make_poles(w.kT, w.mu, *ham.spectral_bounds(), w.n_poles)
+    with pytest.raises(MacroDFTError) as ei:
+        density_matrix_rows(ham, z, wt, w.nodes, w.halfwidth, SolverOptions(method="shifted"))
+    assert ei.value.status == MD_ERR_INVALID
+    rho, e, rows, off = density_matrix_rows(ham, z, wt, w.nodes[:0], w.halfwidth[:0])
+    assert rho.numel() == 0 and rows.numel() == 0 and list(off) == [0]

@@ -169,3 +169,18 @@ def test_mixed_precision_rules(name, n_nodes):
     R = _gpu_rules(w, 40, precision="mixed")
     lam, wts, _ = _oracle_rules(w, 40)
     _compare_fields(w, R, lam, wts, 1e-5, node_err=2.0 ** -24 * np.abs(lam).max())
+
+
+def test_device_deadline_returns_timeout():
+    """The Lanczos kernel's own wall-clock check ends the launch with a
+    timeout status (no fault), and the next call runs normally."""
+    import torch
+    from paper_1907_02604_gb300._lib import MacroDFTError, MD_ERR_TIMEOUT
+    w = make_workload("bulk_mixed").subset(np.arange(64))
+    with pytest.raises(MacroDFTError) as ei:
+        _gpu_rules(w, 40, timeout_s=1e-6)
+    assert ei.value.status == MD_ERR_TIMEOUT
+    torch.cuda.synchronize()
+    R = _gpu_rules(w.subset(np.arange(2)), 8)
+    assert np.all(R.k_used.cpu().numpy() == 8)
+    assert np.all(np.abs(R.weight.cpu().numpy().sum(axis=1) - 1.0) < 1e-12)
