@@ -321,7 +321,7 @@ md_status md_density_adjoint(const md_hamiltonian* ham, const md_poles* poles,
  * ->block are ignored).
  *   - Limits: n_nodes <= MD_NOALLOC_MAX_NODES, P <= MD_NOALLOC_MAX_POLES,
  *     n_nodes * P <= MD_NOALLOC_MAX_SYSTEMS, and one region's Krylov slot
- *     (48 B per point mixed, 64 B per point FP64) within
+ *     (56 B per point mixed, 64 B per point FP64) within
  *     MD_NOALLOC_SCRATCH_BYTES; beyond them it returns MD_ERR_INVALID with
  *     nothing launched.  Concurrency is one CTA per SM, capped by the number
  *     of slots that fit, so large regions run on fewer SMs.

@@ -128,6 +128,9 @@ struct Geo {
     int plane;
     int src;
     FastDiv div_row, div_plane;
+    // per region point: (local slots of its projector atoms, 8 bits each,
+    // 0xFF ends the list; first CSR entry), or null for the CSR lists alone
+    const uint2* nl_rec = nullptr;
 };
 
 template <class R>
@@ -378,6 +381,35 @@ __device__ __forceinline__ int local_slot(const SolveParams& P, const Shared& S,
     return -1;
 }
 
+// The nonlocal term's per-point record for the current region (collect_local_atoms
+// first): the local slots of the point's projector atoms packed into .x and
+// its first CSR entry in .y, so that an apply needs one coalesced load
+// before the values instead of the point's CSR pointer, atom ids and slot
+// lookups in turn.  Points with more than four atoms or an atom outside
+// slots 0..254 get .y = 0xFFFFFFFF and keep the CSR path.
+__device__ void build_nl_records(const SolveParams& P, const Geo& G, const Shared& S, uint2* __restrict__ rec) {
+    for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
+        const int c = (int)fdiv((uint32_t)i, G.div_plane);
+        const int rem = i - c * G.plane;
+        const int b = (int)fdiv((uint32_t)rem, G.div_row);
+        const int a = rem - b * G.m[0];
+        const int gx = wrap_once(G.lo[0] + a, P.n[0]);
+        const int gy = wrap_once(G.lo[1] + b, P.n[1]);
+        const int gz = wrap_once(G.lo[2] + c, P.n[2]);
+        const long long gi = gx + (long long)P.n[0] * (gy + (long long)P.n[1] * gz);
+        const int e0 = __ldg(P.pl_ptr + gi), e1 = __ldg(P.pl_ptr + gi + 1);
+        uint32_t sl = 0xFFFFFFFFu;
+        bool ok = e1 - e0 <= 4;
+        for (int e = e0; ok && e < e1; ++e) {
+            const int k = local_slot(P, S, __ldg(P.pl_atom + e));
+            ok = k >= 0 && k < 0xFF;
+            const int sh = 8 * (e - e0);
+            if (ok) sl = (sl & ~(0xFFu << sh)) | ((uint32_t)k << sh);
+        }
+        rec[i] = make_uint2(sl, ok ? (uint32_t)e0 : 0xFFFFFFFFu);
+    }
+}
+
 // c_al = E_l dV sum_{i in region} p_al(i) v(i): warp per local atom, lane
 // per window row (v, w).  The Gaussian is separable, so each row needs only
 // A = sum_u g_x(u) v and B = sum_u d_x(u) g_x(u) v over its in-sphere run:
@@ -576,6 +608,25 @@ __device__ __forceinline__ C matvec_point(const SolveParams& P, const Geo& G, co
                 yx += w * sx;
                 yy += w * sy;
             }
+        }
+    }
+    if (kNl && P.nonlocal && G.nl_rec) {
+        const uint2 rc = G.nl_rec[i];
+        if (rc.y != 0xFFFFFFFFu) {
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const uint32_t k = (rc.x >> (8 * l)) & 0xFFu;
+                if (k == 0xFFu) break;
+                R f[4];
+                PVal<R>::get(P, (int)rc.y + l, f);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const auto cc = PVal<R>::c(S, (int)k, q);
+                    yx += f[q] * (R)cc.x;
+                    yy += f[q] * (R)cc.y;
+                }
+            }
+            return VMake<C>::make(yx, yy);
         }
     }
     if (kNl && P.nonlocal) {

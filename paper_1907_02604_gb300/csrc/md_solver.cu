@@ -186,6 +186,11 @@ __global__ void __launch_bounds__(kMinB == 1 ? 1024 : 512, kMinB) k_cocg(const _
         if (P.ckpt) x = P.ckpt + P.ckpt_sys_off[out_idx];
 
         if (P.nonlocal) collect_local_atoms(P, G, S);
+        if (Mode::kMixed && P.nonlocal) {   // point records after the vectors
+            uint2* rec = reinterpret_cast<uint2*>(reinterpret_cast<double2*>(dx + P.n_max) + P.n_max);
+            build_nl_records(P, G, S, rec);
+            G.nl_rec = rec;
+        }
         if (P.multishift)
             for (int k = threadIdx.x; k < P.P; k += blockDim.x) {
                 S.sh_pi_prev[k] = make_double2(1.0, 0.0);
@@ -1119,7 +1124,7 @@ cudaError_t launch_cocg_zm(const SolveParams& P, int K, int grid, int block, siz
 
 size_t slot_bytes_for(int precision, long long n_max) {
     const size_t nm = (size_t)((n_max + 63) / 64 * 64);
-    if (precision == MD_PREC_MIXED) return nm * (4 * sizeof(float2) + sizeof(double2));
+    if (precision == MD_PREC_MIXED) return nm * (4 * sizeof(float2) + sizeof(double2) + sizeof(uint2));
     return nm * (3 * sizeof(double2) + sizeof(double2));
 }
 
