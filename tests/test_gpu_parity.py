@@ -187,3 +187,19 @@ def test_fewest_and_most_poles(n_poles):
         g = gpu_run(w, precision="fp64", method=method)
         assert rel_err(g["rho"], o.rho) <= FP64_BAR, method
         assert rel_err(g["e"], o.e_node) <= FP64_BAR, method
+
+
+@pytest.mark.parametrize("method", ["cocg", "shifted"])
+def test_mixed_points_over_four_projector_atoms(method):
+    """Twelve atoms in a 9-bohr cell: in every 9^3 region some points lie in
+    the spheres of more than four atoms (the solver's CSR path) and the rest
+    in at most four (its per-point records); both meet the mixed bar."""
+    w = make_workload("tiny", shape=(18, 18, 18), spacing=(0.5, 0.5, 0.5), fd_order=8, s=4,
+                      nonlocal_proj=True, n_atoms=12, n_nodes=4)
+    # 32 poles at kT = 0.05 resolve f on this cell's wide spectrum (the
+    # densities are within 1e-3 of the dense f(H)_jj)
+    w.n_poles, w.kT, w.mu, w.tol = 32, 0.05, 2.0, 1e-11
+    g = gpu_run(w, precision="mixed", method=method)
+    _, o = oracle_run(w)
+    assert rel_err(g["rho"], o.rho) <= MIXED_BAR
+    assert rel_err(g["e"], o.e_node) <= MIXED_BAR
