@@ -50,6 +50,7 @@ TRAFFIC_SOURCES = ("paper_1907_02604_gb300/csrc/md_solver.cu", "paper_1907_02604
                    "paper_1907_02604_gb300/csrc/md_operator.cuh")
 TRAFFIC_FINGERPRINT = "15df601444a11d3a:c156daa5b1c36f8f:6685de8068da134b:0fb5570fc87854c8:d8fb1f8a14608a26"
 FLOPS_PER_POINT_ITER_8TH = 200.0
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, vendor figure (context beside the measured copy peak)
 
 
 def parse():
@@ -70,6 +71,9 @@ def parse():
     ap.add_argument("--no-shifted", action="store_true", help="skip the shifted-COCG side measurement")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the FP64-form side measurement")
     ap.add_argument("--no-lssgq", action="store_true", help="skip the Lanczos-quadrature side measurement")
+    ap.add_argument("--locality", default="", metavar="S1,S2,...",
+                    help="print the locality report (rho_j against region half-width s) instead of timing")
+    ap.add_argument("--locality-nodes", type=int, default=16)
     return ap.parse_args()
 
 
@@ -219,11 +223,54 @@ def run_reference(args, world, rank):
     print(json.dumps(out), flush=True)
 
 
+def run_locality(args, rank, local):
+    """rho_j and e_j of the same nodes as the region half-width s grows (the
+    analogue of the paper's convergence of the nodal fields with cluster
+    size, Section 4), FP64 solves at tol 1e-10, each s reported against the
+    largest: the truncation error of the local evaluation, not a parity
+    figure.  Rank 0 only."""
+    if rank != 0:
+        return
+    import torch
+    torch.cuda.set_device(local)
+    from synthetic import make_workload
+    from paper_1907_02604_gb300 import Hamiltonian, SolverOptions, density, make_poles
+    w = make_workload(args.workload)
+    s_list = sorted({int(t) for t in args.locality.split(",")})
+    c = w.node_coords()
+    ok = np.ones(len(w.nodes), bool)
+    for d in range(3):   # every region inside the open axes at the largest s
+        if not w.periodic[d]:
+            ok &= (c[:, d] - s_list[-1] >= 0) & (c[:, d] + s_list[-1] < w.shape[d])
+    nodes = w.nodes[np.nonzero(ok)[0][:args.locality_nodes]]
+    ham = Hamiltonian.from_workload(w)
+    z, wt = make_poles(w.kT, w.mu, *ham.spectral_bounds(), w.n_poles)
+    res = {}
+    for s in s_list:
+        hw = np.full(len(nodes), s, np.int32)
+        rho, e, st = density(ham, z, wt, nodes, hw, SolverOptions(tol=1e-10, precision="fp64"), energy=True)
+        res[s] = (rho.cpu().numpy(), e.cpu().numpy(), st)
+    r_ref, e_ref, _ = res[s_list[-1]]
+    curve = []
+    for s in s_list:
+        rho, e, st = res[s]
+        dims = [w.shape[d] if (w.periodic[d] and 2 * s + 1 >= w.shape[d]) else 2 * s + 1 for d in range(3)]
+        curve.append({"s": s, "region": "x".join(map(str, dims)),
+                      "rho_max_rel_diff": float(np.abs(rho - r_ref).max() / np.abs(r_ref).max()),
+                      "e_max_rel_diff": float(np.abs(e - e_ref).max() / np.abs(e_ref).max()),
+                      "iters_mean": float(st["iters_mean"]), "converged": int(st["n_converged"])})
+    print(json.dumps({"report": "locality", "workload": w.name, "nodes": len(nodes), "poles": w.n_poles,
+                      "precision": "fp64", "tol": 1e-10, "reference_s": s_list[-1], "curve": curve}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local, dist = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.locality:
+        run_locality(args, rank, local)
         return
     import torch
     torch.cuda.set_device(local)
@@ -453,6 +500,7 @@ def main():
         "point_iters_per_s": point_iters * world / (el_ms / 1e3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                      "algorithmic_bytes_per_launch": point_iters * B / len(stats),
                      "kernel": "k_cocg<MixedMode>" if prec == "mixed" else "k_cocg<FP64Mode>",
                      "bytes_per_point_iter": B, "peak_kind": peak_kind},

@@ -203,3 +203,16 @@ def test_mixed_points_over_four_projector_atoms(method):
     _, o = oracle_run(w)
     assert rel_err(g["rho"], o.rho) <= MIXED_BAR
     assert rel_err(g["e"], o.e_node) <= MIXED_BAR
+
+
+def test_region_halfwidth_sweep_matches_oracle():
+    """The locality sweep (s = 1 .. the whole cell) through the C ABI: every
+    half-width agrees with the oracle, so the truncation curve the GPU
+    reports is the oracle's."""
+    w = make_workload("tiny", shape=(16, 16, 16), spacing=(0.5, 0.5, 0.5), fd_order=4, n_atoms=8, n_nodes=4, s=1)
+    w.n_poles, w.kT, w.mu, w.tol = 32, 1.0, 2.0, 1e-11
+    for s in (1, 3, 5, 8):
+        w.halfwidth = np.full(len(w.nodes), s, np.int32)
+        g = gpu_run(w, precision="fp64")
+        _, o = oracle_run(w)
+        assert rel_err(g["rho"], o.rho) <= FP64_BAR, s
