@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-shifted", action="store_true", help="skip the shifted-COCG side measurement")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the FP64-form side measurement")
     ap.add_argument("--no-lssgq", action="store_true", help="skip the Lanczos-quadrature side measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint side measurement")
     ap.add_argument("--locality", default="", metavar="S1,S2,...",
                     help="print the locality report (rho_j against region half-width s) instead of timing")
     ap.add_argument("--locality-nodes", type=int, default=16)
@@ -433,6 +434,54 @@ def main():
         lssgq["note"] = ("Lanczos Gauss rules + fields at (mu, kT); host-timed, includes the per-call "
                          "work-list upload and status read-back")
 
+    # ---- side measurement: the adjoint (dL/dV and forces) on the adjoint ---
+    # workload in FP64: the forward solve keeping a checkpoint, the
+    # checkpointed adjoint pass, and the fused one-pass form (host-timed
+    # calls, like the LSSGQ figures)
+    adjoint = None
+    if not args.no_adjoint:
+        from paper_1907_02604_gb300 import Workspace, density_adjoint, density_fused_adjoint
+        wa = make_workload("adjoint_fp64")
+        sl = batch_slice(len(wa.nodes), min(32, len(wa.nodes)), world, rank, 0)
+        nd_a, hw_a = wa.nodes[sl], wa.halfwidth[sl]
+        ham_a = Hamiltonian.from_workload(wa, stream=stream)
+        za, wta = make_poles(wa.kT, wa.mu, *ham_a.spectral_bounds(stream=stream), wa.n_poles)
+        opts_a = SolverOptions(tol=wa.tol, maxit=wa.maxit, precision="fp64")
+        ones = torch.ones(len(nd_a), dtype=torch.float64, device="cuda")
+        ws = Workspace(ham_a, nd_a, hw_a, wa.n_poles)
+
+        def fwd():
+            return density(ham_a, za, wta, nd_a, hw_a, opts_a, energy=True, checkpoint=ws, stream=stream)
+
+        def adj():
+            return density_adjoint(ham_a, za, wta, nd_a, hw_a, ones, ones, opts_a, checkpoint=ws, forces=True,
+                                   stream=stream)
+
+        def fused():
+            return density_fused_adjoint(ham_a, za, wta, nd_a, hw_a, ones, ones, opts_a, forces=True, stream=stream)
+
+        def timed(fn):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            return out, time.perf_counter() - t0
+
+        fwd(), adj(), fused()   # warm-up
+        _, t_fwd = timed(fwd)
+        (g_c, F_c), t_adj = timed(adj)
+        (_, _, g_f, F_f, _), t_fused = timed(fused)
+        pts = int(np.sum((2 * hw_a.astype(np.int64) + 1) ** 3))
+        adjoint = {"workload": wa.name, "systems": len(nd_a) * wa.n_poles, "precision": "fp64",
+                   "forward_with_checkpoint_ms": 1e3 * t_fwd, "adjoint_pass_ms": 1e3 * t_adj,
+                   "fused_forward_adjoint_ms": 1e3 * t_fused, "adjoint_over_forward": t_adj / t_fwd,
+                   "adjoint_checkpoint_read_GB_s": pts * wa.n_poles * 16 / t_adj / 1e9,
+                   "max_rel_diff_dLdV_fused_vs_checkpointed": float((g_f - g_c).abs().max() / g_c.abs().max()),
+                   "max_rel_diff_forces_fused_vs_checkpointed": float((F_f - F_c).abs().max() / F_c.abs().max()),
+                   "note": "dL/drho = dL/de = 1 on every node, forces on every atom; host-timed calls"}
+        ws.close()
+        ham_a.close()
+
     # ---- end to end through the C ABI from host buffers -------------------
     e2e = None
     if not args.no_e2e:
@@ -509,6 +558,7 @@ def main():
         "shifted_cocg": shifted,
         "fp64_form": fp64_form,
         "lssgq": lssgq,
+        "adjoint": adjoint,
         "gpu_launches": 2 * args.steps,
         "launch_shape": {"threads_per_cta": shape[0], "ctas": shape[1]},
         "clocks": clocks,
