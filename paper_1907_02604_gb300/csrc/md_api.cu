@@ -1037,7 +1037,7 @@ extern "C" md_status md_lssgq_rules(const md_hamiltonian* ham, const md_nodes* n
     P.timeout_ns = opts->timeout_s > 0 ? (unsigned long long)(opts->timeout_s * 1e9) : 0ULL;
     P.n_max = (int)((R.n_max + 63) / 64 * 64);
     const size_t elem = opts->precision == MD_PREC_MIXED ? sizeof(float) : sizeof(double);
-    P.slot_bytes = ((size_t)2 * P.n_max * elem + 511) / 512 * 512;
+    P.slot_bytes = ((size_t)2 * P.n_max * elem + (size_t)P.n_max * sizeof(uint2) + 511) / 512 * 512;
 
 #define LTRY(expr)                                                                                   \
     do {                                                                                             \

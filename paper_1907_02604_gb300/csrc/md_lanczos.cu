@@ -94,7 +94,12 @@ __global__ void __launch_bounds__(1024) k_lanczos(const __grid_constant__ SolveP
         G.div_plane = make_fastdiv((uint32_t)G.plane);
         const long long base = (long long)node * L.K;
 
-        if (P.nonlocal) collect_local_atoms(P, G, S);
+        if (P.nonlocal) {
+            collect_local_atoms(P, G, S);
+            uint2* rec = reinterpret_cast<uint2*>(u1 + P.n_max);   // point records after the vectors
+            build_nl_records(P, G, S, rec);
+            G.nl_rec = rec;
+        }
         R* uc = u0;
         R* up = u1;
         for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
