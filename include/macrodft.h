@@ -356,7 +356,7 @@ typedef struct {
     double breakdown_tol;  /* stop early when beta_k <= tol (|alpha_1| + beta_1 + 1),
                               the Krylov space being invariant (0 = 1e-13) */
     double timeout_s;      /* device wall-clock budget, 0 = none */
-    int32_t block;         /* threads per CTA, 0 = 512; multiple of 32 in 64..1024 */
+    int32_t block;         /* threads per CTA, 0 = 1024; multiple of 32 in 64..1024 */
     int32_t precision;     /* MD_PREC_FP64: FP64 Lanczos vectors and arithmetic;
                               MD_PREC_MIXED: FP32 vectors, stencil and projector
                               terms with compensated FP32 partial sums, FP64
