@@ -25,6 +25,13 @@
  *   - Complex numbers are interleaved doubles (re, im).
  *   - Requires an sm_103a GPU; every compute entry point returns
  *     MD_ERR_CUDA when no such device is present.
+ *   - Threads: calls on different Hamiltonian handles may run from
+ *     different host threads at once.  Calls on one handle that solve
+ *     (md_density, md_energy, md_density_adjoint, md_density_fused_adjoint,
+ *     md_density_matrix_rows, md_lssgq_rules) share scratch the handle
+ *     caches, so issue them from one thread at a time; each of them ends
+ *     synchronised with its stream, so consecutive calls never overlap on
+ *     the GPU.  A plan (md_plan_create) owns its own scratch.
  */
 #ifndef MACRODFT_H
 #define MACRODFT_H

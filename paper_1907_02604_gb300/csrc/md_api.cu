@@ -306,12 +306,14 @@ std::vector<Shape> candidate_shapes(const md_plan* pl, bool zm_ok, int max_plane
 // sample of systems with a short iteration cap and keeps the one with the
 // most region-point iterations per second.  Results are cached per
 // (precision, stencil width, region-size bucket, nonlocal, z-march
-// eligibility) for the life of the process.
+// eligibility, device) for the life of the process; plans may be created
+// from several host threads, so the cache is guarded (two threads tuning the
+// same key at once both run their trials and store the same kind of answer).
 struct TuneKey {
-    int precision, q, bucket, nonlocal, zm;
+    int precision, q, bucket, nonlocal, zm, device;
     bool operator==(const TuneKey& o) const {
         return precision == o.precision && q == o.q && bucket == o.bucket && nonlocal == o.nonlocal &&
-               zm == o.zm;
+               zm == o.zm && device == o.device;
     }
 };
 struct TuneEntry {
@@ -319,16 +321,22 @@ struct TuneEntry {
     Shape shape;
 };
 std::vector<TuneEntry> g_tune_cache;
+std::mutex g_tune_mutex;
 
 md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_t scratch_bytes,
                    Shape& out) {
+    int dev = 0;
+    cudaGetDevice(&dev);
     const TuneKey key{pl->precision, pl->P.q, (int)((pl->P.n_max + 4095) / 4096), pl->P.nonlocal,
-                      (cands.size() > 2 ? 1 : 0) + 2 * pl->P.multishift};
-    for (const auto& e : g_tune_cache)
-        if (e.key == key) {
-            out = e.shape;
-            return MD_OK;
-        }
+                      (cands.size() > 2 ? 1 : 0) + 2 * pl->P.multishift, dev};
+    {
+        std::lock_guard<std::mutex> guard(g_tune_mutex);
+        for (const auto& e : g_tune_cache)
+            if (e.key == key) {
+                out = e.shape;
+                return MD_OK;
+            }
+    }
     const long long nw = pl->P.n_sys;   // work items (systems, or nodes with shifted COCG)
     int max_per = 1;
     for (const auto& c : cands) max_per = std::max(max_per, c.per_sm);
@@ -407,7 +415,10 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
         }
     }
     cudaFree(d_sample);
-    g_tune_cache.push_back(TuneEntry{key, bs});
+    {
+        std::lock_guard<std::mutex> guard(g_tune_mutex);
+        g_tune_cache.push_back(TuneEntry{key, bs});
+    }
     out = bs;
     return MD_OK;
 }
