@@ -81,3 +81,26 @@ def test_make_poles_rejects_bad_input(lib):
 def test_version_and_error_string(lib):
     assert b"sm_103a" in lib.md_version()
     assert isinstance(lib.md_last_error(), bytes)
+
+
+def test_region_size_matches_oracle_regions():
+    """The binding's region size (it lays out the density-matrix rows) equals
+    the oracle's region for windows, whole-axis rings and open axes."""
+    from types import SimpleNamespace
+
+    from oracle import hamiltonian as oh
+    from paper_1907_02604_gb300.api import _region_size
+    from synthetic import make_workload
+    rng = np.random.default_rng(3)
+    for shape, periodic in (((9, 10, 11), (True, True, True)), ((6, 12, 8), (True, True, True)),
+                            ((14, 12, 16), (False, True, False))):
+        w = make_workload("tiny", shape=shape, periodic=periodic)
+        ham = SimpleNamespace(shape=shape, periodic=periodic)
+        for _ in range(40):
+            s = int(rng.integers(0, 8))
+            node = int(rng.integers(0, int(np.prod(shape))))
+            try:
+                reg = oh.region_of(w, node, s)
+            except ValueError:   # leaves an open axis: the library refuses it too
+                continue
+            assert _region_size(ham, node, s) == int(np.prod(reg.dims)), (shape, periodic, node, s)
