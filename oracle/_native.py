@@ -18,6 +18,9 @@ _handle = None
 
 
 def build(force: bool = False) -> str:
+    """Compile the oracle's plain C COCG (gcc, OpenMP) into oracle/_build
+    if it is missing or older than its source; returns the library path.
+    Test infrastructure: nothing on the product path calls it."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
     if force or stale:
@@ -29,6 +32,8 @@ def build(force: bool = False) -> str:
 
 
 def load_cocg():
+    """The compiled oracle COCG (built on first use), loaded once per
+    process."""
     global _handle
     with _lock:
         if _handle is None:

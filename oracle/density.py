@@ -30,6 +30,10 @@ from ._native import load_cocg
 
 @dataclass
 class OracleHamiltonian:
+    """The discrete Hamiltonian of Section 2.1 (Eq. Hamiltonian) as the
+    oracle holds it: local potential on the grid (or on requested points),
+    the nonlocal projectors, the FD kinetic stencil and the spectral
+    interval [emin, emax] the poles are built on."""
     V: np.ndarray
     projs: list
     stencil: ham_mod.Stencil
@@ -65,11 +69,17 @@ def region_points(w) -> list:
 
 
 def poles_for(w, H: OracleHamiltonian):
+    """The P poles and weights of the rational Fermi expansion (contour
+    quadrature, see oracle/poles.py) on the Hamiltonian's spectral interval,
+    at the workload's kT and mu."""
     return poles_mod.fermi_poles(w.kT, w.mu, H.emin, H.emax, w.n_poles)
 
 
 @dataclass
 class OracleResult:
+    """Per-node density and band energy (Eq. Electron_density:GQ with the
+    pole expansion; first term of Eq. tot), with each (node, pole) solve's
+    x_jp(j), iteration count, residual and status."""
     rho: np.ndarray        # (n_nodes,)
     e_node: np.ndarray     # (n_nodes,)
     x_src: np.ndarray      # (n_nodes, P) complex

@@ -51,6 +51,9 @@ class Stencil:
 
 
 def kinetic_stencil(spacing, order: int) -> Stencil:
+    """-1/2 of the FD Laplacian (Section 2.1's finite-difference
+    discretisation) per axis: off-centre coefficients for offsets 1..q and
+    the constant diagonal, from the central second-derivative weights."""
     w = fd_second_derivative_weights(order)
     q = order // 2
     coef = np.zeros((3, q))
@@ -155,6 +158,9 @@ def local_potential_gradient_terms(w, a: int):
 
 @dataclass
 class Projector:
+    """One nonlocal projector p_al of atom a (an s or p Gaussian, zero
+    beyond the cutoff radius): its grid support, its normalised values there
+    and its energy E_l."""
     idx: np.ndarray    # grid indices of the support (r <= rc)
     val: np.ndarray    # normalised values there
     energy: float      # E_l
@@ -218,6 +224,10 @@ class Region:
 
 
 def region_of(w, node: int, s: int) -> Region:
+    """The truncation region R(j) of a node (Section 2.1's locality): the
+    cube of side 2s+1 centred on it with H restricted to it (Dirichlet
+    faces), wrapped on periodic axes, the whole axis as a ring where 2s+1
+    reaches the axis length; raises if the cube leaves a non-periodic axis."""
     nx, ny, nz = w.shape
     c = (node % nx, (node // nx) % ny, node // (nx * ny))
     axes = []

@@ -53,6 +53,8 @@ class RegionOperator:
         self.projs = ham_mod.projectors_in_region(H.projs, region, w.n_grid)
 
     def apply(self, v):
+        """H_R v on the region (stencil with Dirichlet faces or ring wrap,
+        local potential, projectors restricted to R)."""
         mx, my, mz = self.dims
         u = v.reshape(mz, my, mx)
         out = (self.stencil.diag + self.V.reshape(mz, my, mx)) * u
