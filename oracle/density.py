@@ -180,6 +180,96 @@ def solve(w, H: OracleHamiltonian = None, z=None, wts=None, tol: float = 1e-12,
                         z=z, wts=wts, regions=regions, x_full=xf)
 
 
+def entropy_node(res: OracleResult, w_entropy, kT: float) -> np.ndarray:
+    """Entropy term per node (the last term of Eq. tot taken at node j,
+    g ln g + (1-g) ln(1-g) replaced by the rational form of -phi_S built on
+    the solve's own poles, poles.entropy_weights):
+        s_j = 2 kT sum_p Im( w^S_p x_jp(j) )  ~=  2 kT [phi_S(H_R)]_jj >= 0."""
+    return 2.0 * kT * np.imag(np.asarray(w_entropy)[None, :] * res.x_src).sum(axis=1)
+
+
+def free_energy_terms(w, res: OracleResult, w_entropy, node_weight=None) -> dict:
+    """Node-weighted totals of the cluster-sampled energy (Section 3, Eqs.
+    free_cg and free_cg_sampling: E ~= sum_q n_q (1/N_q) sum_{p in C_q} F_p),
+    here sum_j nu_j F_j over the nodes with weights nu_j (1 if None):
+        n_electrons = dV sum_j nu_j rho_j        (Eq. Fermi:Rho)
+        e_band      = sum_j nu_j e_j             (first term of Eq. tot)
+        ts          = sum_j nu_j s_j             (entropy term, >= 0)
+        free_energy = e_band - ts                (Mermin: E - TS)."""
+    nu = np.ones(len(res.rho)) if node_weight is None else np.asarray(node_weight, dtype=np.float64)
+    s = entropy_node(res, w_entropy, w.kT)
+    n_e = float(w.dV * np.sum(nu * res.rho))
+    eb = float(np.sum(nu * res.e_node))
+    ts = float(np.sum(nu * s))
+    return {"n_electrons": n_e, "e_band": eb, "ts": ts, "free_energy": eb - ts, "s_node": s}
+
+
+def cluster_sampling(w, esp_nodes, n_q, radius: float):
+    """Nodes and weights of the cluster-sampled energy (Section 3, Eq.
+    free_cg with Eq. free_cg_sampling): C_q is the set of fine-grid points
+    within `radius` (bohr; minimum image on periodic axes) of the q-th
+    sampling point, N_q = |C_q|, and every p in C_q carries n_q / N_q, so
+    that sum_p nu_p F_p = sum_q n_q (1/N_q) sum_{p in C_q} F_p.  Points in
+    several clusters appear once with their weights summed.  Returns
+    (nodes ascending, nu)."""
+    esp_nodes = np.asarray(esp_nodes, dtype=np.int64)
+    n_q = np.asarray(n_q, dtype=np.float64)
+    nx, ny, nz = w.shape
+    h = np.asarray(w.spacing, dtype=np.float64)
+    acc = {}
+    for q, g in enumerate(esp_nodes):
+        c = np.array([g % nx, (g // nx) % ny, g // (nx * ny)])
+        reach = np.floor(radius / h).astype(int) + 1
+        o = np.stack(np.meshgrid(*[np.arange(-r, r + 1) for r in reach], indexing="ij"), -1).reshape(-1, 3)
+        o = o[np.sum((o * h) ** 2, axis=1) <= radius * radius]
+        p = c[None, :] + o
+        keep = np.ones(len(p), bool)
+        for d in range(3):
+            if w.periodic[d]:
+                p[:, d] %= w.shape[d]      # every image in the ball: the minimum one is among them
+            else:
+                keep &= (p[:, d] >= 0) & (p[:, d] < w.shape[d])
+        pts = np.unique(p[keep, 0] + nx * (p[keep, 1] + ny * p[keep, 2]))
+        for pt in pts:
+            acc[int(pt)] = acc.get(int(pt), 0.0) + n_q[q] / len(pts)
+    nodes = np.array(sorted(acc), dtype=np.int64)
+    return nodes, np.array([acc[int(p)] for p in nodes])
+
+
+def electron_count_poles(w, H: OracleHamiltonian, mu: float, node_weight=None, tol: float = 1e-12) -> float:
+    """N(mu) = dV sum_j nu_j rho_j(mu) (Eq. Fermi:Rho with g -> r), each
+    rho_j(mu) from a fresh pole set built at mu on H's spectral interval
+    (nu_j = 1 if node_weight is None: every grid point a node)."""
+    z, wts = poles_mod.fermi_poles(w.kT, mu, H.emin, H.emax, w.n_poles)
+    res = solve(w, H, z=z, wts=wts, tol=tol)
+    nu = np.ones(len(res.rho)) if node_weight is None else np.asarray(node_weight, dtype=np.float64)
+    return float(w.dV * np.sum(nu * res.rho))
+
+
+def fermi_level_poles(w, H: OracleHamiltonian, n_electrons: float, node_weight=None, mu_tol: float = 1e-11,
+                      tol: float = 1e-12):
+    """Fermi level of the pole form: the mu with electron_count_poles(mu) =
+    n_electrons, by bisection on [emin, emax] (N rises from ~0 to ~2 sum nu
+    across the interval) until the bracket is narrower than mu_tol.  Returns
+    (mu, N(mu), evaluations)."""
+    lo, hi = H.emin, H.emax
+    n_lo = electron_count_poles(w, H, lo, node_weight, tol) - n_electrons
+    n_hi = electron_count_poles(w, H, hi, node_weight, tol) - n_electrons
+    if n_lo > 0 or n_hi < 0:
+        raise ValueError("n_electrons is outside the count range on the spectral interval")
+    evals = 2
+    while hi - lo > mu_tol:
+        mid = 0.5 * (lo + hi)
+        n_mid = electron_count_poles(w, H, mid, node_weight, tol) - n_electrons
+        evals += 1
+        if n_mid < 0:
+            lo = mid
+        else:
+            hi = mid
+    mu = 0.5 * (lo + hi)
+    return mu, electron_count_poles(w, H, mu, node_weight, tol), evals + 1
+
+
 def density_matrix_rows(res: OracleResult) -> list:
     """Row j of the density matrix over R(j) (Eq. dm in the grid basis, g
     replaced by r): gamma_jk = sum_p Im(w_p x_jp(k)); rho_j = (2/dV) gamma_jj."""

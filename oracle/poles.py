@@ -33,6 +33,10 @@ follows (x = eps - mu, a = (pi kT)^2, spectrum x in [-dE, dE]):
        z = mu + xi_j,        w = c_j g(xi_j)
        z = mu - conj(xi_j),  w = conj(c_j g(-xi_j))
    so P = N shifted solves.  The error decays like exp(-pi K' N / (4K)).
+6. Nothing above uses more of g than its analyticity off the rays of the
+   imaginary axis beyond +-i pi kT.  The entropy function of Eq. (tot)'s last
+   term has its branch points at the same Matsubara points, so the same
+   nodes with weights c_j phi_S(+-xi_j) approximate it (entropy_weights).
 
 Library primitives used as steps: scipy.special.ellipk / ellipkm1 (complete
 elliptic integrals) and scipy.special.ellipj (Jacobi functions of a real
@@ -70,8 +74,51 @@ def _sn_cn_dn(t: complex, m: float, m1: float):
     return sn, cn, dn
 
 
-def fermi_poles(kT: float, mu: float, emin: float, emax: float, P: int):
-    """Poles z (complex128[P], Im > 0) and weights w (complex128[P])."""
+def _log1p_c(u):
+    """log(1 + u) for complex u with |u| < 1, accurate also for tiny |u|
+    (numpy's complex log1p forms 1 + u first): the alternating series
+    sum_k (-1)^(k+1) u^k / k to k = 16 where |u| < 0.1 (truncation below
+    0.1^17/17), log(1 + u) elsewhere."""
+    u = np.asarray(u, dtype=np.complex128)
+    out = np.log(1.0 + u)
+    small = np.abs(u) < 0.1
+    us = u[small]
+    acc = np.zeros_like(us)
+    for k in range(16, 0, -1):      # Horner form of the series
+        acc = us * ((1.0 if k % 2 else -1.0) / k + acc)
+    out[small] = acc
+    return out
+
+
+def entropy_fn(x, kT: float):
+    """phi_S(x) = -[f ln f + (1 - f) ln(1 - f)], f = fermi(x, kT): the
+    bracket of the last term of Eq. (tot) with its sign turned so that
+    phi_S >= 0 on the real axis (phi_S(0) = ln 2), for real or complex x.
+
+    With y = x/kT, ln f = -ln(1 + e^y) and ln(1 - f) = y - ln(1 + e^y), so
+    phi_S = ln(1 + e^y) - (1 - f) y.  Written per half-plane so that nothing
+    cancels and every logarithm has its argument in the disc |u - 1| < 1:
+        Re y <= 0:  log1p(e^y)  - y e^y  / (1 + e^y)
+        Re y >  0:  log1p(e^-y) + y e^-y / (1 + e^-y)
+    The two pieces agree on Re y = 0 for |Im y| < pi, so together they are
+    the analytic continuation of phi_S off the rays |Im y| >= pi of the
+    imaginary axis, where its branch points (the Matsubara points) lie."""
+    x = np.asarray(x)
+    y = x.astype(np.complex128) / kT
+    out = np.empty_like(y)
+    pos = y.real > 0
+    en = np.exp(-y[pos])
+    out[pos] = _log1p_c(en) + y[pos] * en / (1.0 + en)
+    ep = np.exp(y[~pos])
+    out[~pos] = _log1p_c(ep) - y[~pos] * ep / (1.0 + ep)
+    if not np.iscomplexobj(x):
+        return out.real
+    return out
+
+
+def _contour_nodes(kT: float, mu: float, emin: float, emax: float, P: int):
+    """Steps 2-4 of the construction: the P/2 trapezoid nodes xi_j (first
+    quadrant) and their factors c_j = h w'(t_j) / (2 pi xi_j)."""
     if P < 2 or P % 2:
         raise ValueError("P must be an even number >= 2")
     if not (kT > 0 and emax > emin):
@@ -86,22 +133,46 @@ def fermi_poles(kT: float, mu: float, emin: float, emax: float, P: int):
     Kp = float(ellipk(kp2))               # K(k') = K'
     h = 4.0 * K / P
     c0 = math.sqrt(m_lo * m_hi)
-    z = np.empty(P, dtype=np.complex128)
-    w = np.empty(P, dtype=np.complex128)
+    xis = np.empty(P // 2, dtype=np.complex128)
+    cs = np.empty(P // 2, dtype=np.complex128)
     for j in range(P // 2):
         t = complex(-K + (j + 0.5) * h, 0.5 * Kp)
         sn, cn, dn = _sn_cn_dn(t, k * k, kp2)
         wq = c0 * (1.0 / k + sn) / (1.0 / k - sn)
         dw = c0 * (2.0 / k) * cn * dn / (1.0 / k - sn) ** 2
-        xi = np.sqrt(wq - a)                # principal root: first quadrant
-        cj = h * dw / (2.0 * math.pi * xi)
-        gp = fermi(np.array([xi]), kT)[0]
-        gm = fermi(np.array([-xi]), kT)[0]
+        xis[j] = np.sqrt(wq - a)            # principal root: first quadrant
+        cs[j] = h * dw / (2.0 * math.pi * xis[j])
+    return xis, cs
+
+
+def _poles_for_function(phi, kT: float, mu: float, emin: float, emax: float, P: int):
+    """Step 5 for any phi(x) analytic off the Matsubara rays: node j gives
+    z = mu + xi_j with weight c_j phi(xi_j) and z = mu - conj(xi_j) with
+    weight conj(c_j phi(-xi_j))."""
+    xis, cs = _contour_nodes(kT, mu, emin, emax, P)
+    z = np.empty(P, dtype=np.complex128)
+    w = np.empty(P, dtype=np.complex128)
+    for j, (xi, cj) in enumerate(zip(xis, cs)):
         z[2 * j] = mu + xi
-        w[2 * j] = cj * gp
+        w[2 * j] = cj * phi(np.array([xi]), kT)[0]
         z[2 * j + 1] = mu - np.conj(xi)
-        w[2 * j + 1] = np.conj(cj * gm)
+        w[2 * j + 1] = np.conj(cj * phi(np.array([-xi]), kT)[0])
     return z, w
+
+
+def fermi_poles(kT: float, mu: float, emin: float, emax: float, P: int):
+    """Poles z (complex128[P], Im > 0) and weights w (complex128[P])."""
+    return _poles_for_function(fermi, kT, mu, emin, emax, P)
+
+
+def entropy_weights(kT: float, mu: float, emin: float, emax: float, P: int):
+    """Weights w^S (complex128[P]) on the poles of fermi_poles with the same
+    arguments, such that sum_p Im(w^S_p / (eps - z_p)) ~= phi_S(eps - mu)
+    (entropy_fn): step 1's contour integral taken of phi_S instead of g.
+    phi_S has its singularities at the same Matsubara points as g, so the
+    same quadrature nodes serve it and no further solves are needed: the
+    entropy term per node is s_j = 2 kT sum_p Im(w^S_p x_jp(j))."""
+    return _poles_for_function(entropy_fn, kT, mu, emin, emax, P)[1]
 
 
 def rational(eps, z, w):
