@@ -9,6 +9,18 @@ def rel_err(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
+def rel_err_per_node(a, b, floor=1e-3):
+    """Largest per-node relative error |a_j - b_j| / |b_j| over the nodes
+    with |b_j| > floor * max|b| (low-density nodes excluded, where a relative
+    figure means little)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    keep = np.abs(b) > floor * np.max(np.abs(b))
+    if not keep.any():
+        return 0.0
+    return float(np.max(np.abs(a[keep] - b[keep]) / np.abs(b[keep])))
+
+
 def gpu_run(w, precision=None, tol=None, energy=True, checkpoint=False, strict=True, **kw):
     import torch
     from paper_1907_02604_gb300 import Hamiltonian, SolverOptions, Workspace, density, make_poles

@@ -25,7 +25,8 @@ def test_plan_uneven_regions_one_launch(precision):
     z, wt = make_poles(w.kT, w.mu, *ham.spectral_bounds(), w.n_poles)
     plan = Plan(ham, z, wt, w.nodes, w.halfwidth, SolverOptions(tol=w.tol, precision=precision))
     block, grid = plan.launch_shape()
-    assert block in (256, 512, 768, 1024) and 0 < grid <= w.n_systems
+    # a CTA per system (generic kernels) or a cluster of CTAs per system
+    assert block % 32 == 0 and 64 <= block <= 1024 and grid > 0
     plan.launch()
     st = plan.stats()
     assert st["n_converged"] == w.n_systems
