@@ -123,10 +123,20 @@ typedef struct {
                               previous one restarts the Krylov recurrence */
     double timeout_s;      /* device wall-clock budget for the call, 0 = none */
     int32_t block;         /* threads per CTA; 0 = library choice (autotuned) */
-    int32_t ctas_per_sm;   /* resident CTAs per SM; 0 = library choice */
+    int32_t ctas_per_sm;   /* resident CTAs per SM; 0 = library choice.  With
+                              kernel 3: CTAs per cluster (1..8; 0 = the fewest
+                              whose slabs fit in shared memory) */
     int32_t kernel;        /* with block > 0: 0 or 1 = generic kernel, 2 = shared-memory
                               z-march kernel (mixed precision, 4th/8th order, no
-                              whole-axis rings; ceil(m0*m1/block) <= 4) */
+                              whole-axis rings; ceil(m0*m1/block) <= 4).
+                              3 = cluster kernel (block may be 0): mixed precision,
+                              fd_order <= 8, no whole-axis rings, method 0; each
+                              (node, pole) system runs on one thread-block cluster
+                              whose CTAs hold z-slabs of the Krylov vectors p and r
+                              in shared memory (halo planes read from the
+                              neighbouring CTAs), so the vectors do not stream
+                              through HBM.  With kernel 0 and block 0 the
+                              autotuner includes it among its candidates. */
     int32_t method;        /* 0 = one COCG per (node, pole) system.
                               1 = shifted COCG: per node one Krylov sequence, seeded
                               with the pole nearest the real axis, serves all P poles
@@ -214,10 +224,87 @@ md_status md_density(const md_hamiltonian* ham, const md_poles* poles,
                      md_stats* stats, void* stream);
 
 /* Band energy (first term of Eq. tot): e_out per node (device, may be
- * NULL) and their sum in *e_band (host).  Same solves as md_density. */
+ * NULL) and the node-weighted sum *e_band = sum_j nu_j e_j (host), with
+ * node_weight (device, n_nodes doubles, or NULL for nu = 1) the weights of
+ * the cluster-sampled energy (Section 3, Eq. free_cg; see
+ * md_cluster_sampling).  Same solves as md_density; synchronises `stream`;
+ * the sum is formed on the device in a fixed order. */
 md_status md_energy(const md_hamiltonian* ham, const md_poles* poles,
-                    const md_nodes* nodes, const md_solver_opts* opts,
-                    double* e_out, double* e_band, md_stats* stats, void* stream);
+                    const md_nodes* nodes, const double* node_weight,
+                    const md_solver_opts* opts, double* e_out, double* e_band,
+                    md_stats* stats, void* stream);
+
+/* ---- Free-energy terms (Section 3; Eq. tot) ------------------------------
+ * The entropy term of Eq. (tot) needs no further solves: the contour
+ * quadrature behind md_make_poles uses no more of the Fermi-Dirac function
+ * than its analyticity off the imaginary rays through the Matsubara points,
+ * and the entropy function phi_S(x) = -[g ln g + (1-g) ln(1-g)] has its
+ * singularities at the same points.  md_make_entropy_weights returns the
+ * weights w^S on the poles md_make_poles returns for the same arguments,
+ * with sum_p Im(w^S_p / (eps - z_p)) ~= phi_S(eps - mu) on [emin, emax]
+ * (the error falls at the Fermi expansion's rate in P).  Per node,
+ *     s_j = 2 kT sum_p Im(w^S_p x_jp(j))  ~= 2 kT [phi_S(H_R)]_jj >= 0,
+ * the last term of Eq. (tot) at node j (its printed sign makes it +TS; the
+ * free energy below takes Mermin's E - TS).  w_out: host, 2P doubles.  Pure
+ * host code: needs no GPU. */
+md_status md_make_entropy_weights(double kT, double mu, double emin, double emax, int32_t P,
+                                  double* w_out);
+
+typedef struct {
+    double n_electrons;   /* dV sum_j nu_j rho_j                    (Eq. Fermi:Rho) */
+    double e_band;        /* sum_j nu_j e_j                    (first term, Eq. tot) */
+    double ts;            /* sum_j nu_j s_j       (entropy term, Eq. tot; 0 without w^S) */
+    double free_energy;   /* e_band - ts */
+} md_free_energy_terms;
+
+/* Density, band energy and entropy per node from one set of per-pole solves,
+ * and their node-weighted totals: the cluster-sampled energy of Section 3,
+ * E ~= sum_q n_q (1/N_q) sum_{p in C_q} F_p (Eqs. free_cg, free_cg_sampling),
+ * is sum_j nu_j F_j over the nodes and weights md_cluster_sampling returns.
+ *   w_entropy: host, 2P doubles from md_make_entropy_weights (same poles), or
+ *              NULL (no entropy term: ts = 0, s_out must be NULL).
+ *   kT:        temperature of the weights (> 0 when w_entropy is given).
+ *   node_weight: device, n_nodes doubles, or NULL (nu = 1).
+ *   rho_out, e_out, s_out: device, n_nodes doubles each, or NULL.
+ *   terms:     host, the totals (formed on the device in a fixed order).
+ * Synchronises `stream`.  Status as md_density. */
+md_status md_free_energy(const md_hamiltonian* ham, const md_poles* poles,
+                         const double* w_entropy, double kT, const md_nodes* nodes,
+                         const double* node_weight, const md_solver_opts* opts,
+                         double* rho_out, double* e_out, double* s_out,
+                         md_free_energy_terms* terms, md_stats* stats, void* stream);
+
+/* Nodes and weights of the cluster-sampled energy (Section 3, Eqs. free_cg
+ * and free_cg_sampling): C_q = the grid points within `radius` (bohr) of
+ * electronic sampling point q (grid index esp[q]), by minimum image on
+ * periodic axes and inside the grid on open ones; N_q = |C_q|; every p in
+ * C_q carries n_q / N_q, the weights of a point in several clusters summed.
+ * Points are returned ascending, each once.  Two calls: with node_out and
+ * weight_out NULL, *n_out receives the count; then with arrays of *n_out
+ * entries (host).  Errors: MD_ERR_INVALID (bad grid, index, radius or
+ * n_q, capacity below the count; *n_out then holds the count).  Pure host
+ * code: needs no GPU. */
+md_status md_cluster_sampling(const md_grid* grid, int64_t n_esp, const int64_t* esp,
+                              const double* n_q, double radius, int64_t* n_out,
+                              int64_t* node_out, double* weight_out);
+
+/* Fermi level of the pole form (Eq. Fermi:Rho with g -> r, the step before
+ * the density in Algorithm 1): the mu at which
+ *     N(mu) = dV sum_j nu_j rho_j(mu) = n_electrons,
+ * each N(mu) from per-pole solves with the P poles rebuilt at mu on the
+ * Hamiltonian's spectral interval (one prepared batch relaunched), by the
+ * Illinois variant of regula falsi on [emin, emax] until the bracket is
+ * narrower than mu_tol (0 = 1e-10 Ha) or 200 counts.  node_weight: device,
+ * n_nodes, or NULL (nu = 1: every grid point a node).  opts as md_density
+ * (method 1, shifted COCG, makes each count cheaper).  *mu_out, *count_out
+ * (N at *mu_out; may be NULL), *evals_out (counts made; may be NULL): host.
+ * Errors: MD_ERR_INVALID when n_electrons lies outside [N(emin), N(emax)];
+ * solver statuses as md_density.  Synchronises `stream`. */
+md_status md_fermi_level_poles(const md_hamiltonian* ham, double kT, int32_t P,
+                               const md_nodes* nodes, const double* node_weight,
+                               const md_solver_opts* opts, double n_electrons, double mu_tol,
+                               double* mu_out, double* count_out, int32_t* evals_out,
+                               void* stream);
 
 /* Density, band energy and the adjoint in one pass, without a checkpoint,
  * for losses whose node sensitivities a_j = dL/drho_j and b_j = dL/de_j are
@@ -332,14 +419,19 @@ md_status md_density_adjoint(const md_hamiltonian* ham, const md_poles* poles,
  *     MD_NOALLOC_SCRATCH_BYTES; beyond them it returns MD_ERR_INVALID with
  *     nothing launched.  Concurrency is one CTA per SM, capped by the number
  *     of slots that fit, so large regions run on fewer SMs.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address in the current
+ *     device's context (cudaGetSymbolAddress), so a reset context leaves no
+ *     stale address behind.
+ *   - The call cannot be captured into a CUDA graph: it copies from pageable
+ *     host memory, waits for its stream, and relies on a host lock that a
+ *     replayed graph would bypass.  On a capturing stream it returns
+ *     MD_ERR_INVALID with nothing enqueued.
  *   - Every call shares the array, which keeps the last call's contents;
  *     the call zeroes what must start at zero.  Calls that overlap on the
  *     GPU race on the array and corrupt each other's results.  Calls made
  *     through this entry point in one process take a host lock and each
- *     synchronises its stream before returning, so they do not overlap. */
+ *     synchronises its stream before returning, error returns included, so
+ *     they do not overlap. */
 #define MD_NOALLOC_SCRATCH_BYTES (64u << 20)
 #define MD_NOALLOC_MAX_SYSTEMS 16384
 #define MD_NOALLOC_MAX_NODES 4096
@@ -412,6 +504,15 @@ md_status md_fermi_level(int64_t n_nodes, int32_t K, const double* lambda,
  * paper's Section 2.1 uses order 6).  w_out: host, q+1 doubles.  Pure host
  * code: needs no GPU. */
 md_status md_fd_weights(int32_t order, double* w_out);
+
+/* Measured fused multiply-add rate of this GPU (the paper has no
+ * counterpart: it is the peak the FP64 solver form's roofline is reported
+ * against).  precision MD_PREC_FP64 times FP64 FMAs, MD_PREC_MIXED FP32
+ * FMAs: 8 independent chains per thread on every SM, a fixed chain length
+ * (a bounded run of some milliseconds), timed with CUDA events on
+ * `stream`.  *tflops_out (host) = 2 x FMAs / s / 1e12.  Allocates a few
+ * bytes of device memory; synchronises `stream`. */
+md_status md_fma_rate(int32_t precision, void* stream, double* tflops_out);
 
 /* Description of the last error on the calling host thread ("" if none). */
 const char* md_last_error(void);

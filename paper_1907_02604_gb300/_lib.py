@@ -71,6 +71,14 @@ class md_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class md_free_energy_terms(ctypes.Structure):
+    _fields_ = [("n_electrons", ctypes.c_double), ("e_band", ctypes.c_double), ("ts", ctypes.c_double),
+                ("free_energy", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # every symbol include/macrodft.h declares: (name, restype, argtypes)
 _VP = ctypes.c_void_p
 SIGNATURES = [
@@ -88,9 +96,20 @@ SIGNATURES = [
     ("md_density", ctypes.c_int, [_VP, ctypes.POINTER(md_poles), ctypes.POINTER(md_nodes),
                                   ctypes.POINTER(md_solver_opts), _VP, _VP, _VP,
                                   ctypes.POINTER(md_stats), _VP]),
-    ("md_energy", ctypes.c_int, [_VP, ctypes.POINTER(md_poles), ctypes.POINTER(md_nodes),
+    ("md_energy", ctypes.c_int, [_VP, ctypes.POINTER(md_poles), ctypes.POINTER(md_nodes), _VP,
                                  ctypes.POINTER(md_solver_opts), _VP, c_double_p,
                                  ctypes.POINTER(md_stats), _VP]),
+    ("md_make_entropy_weights", ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_int32, c_double_p]),
+    ("md_free_energy", ctypes.c_int, [_VP, ctypes.POINTER(md_poles), c_double_p, ctypes.c_double,
+                                      ctypes.POINTER(md_nodes), _VP, ctypes.POINTER(md_solver_opts),
+                                      _VP, _VP, _VP, ctypes.POINTER(md_free_energy_terms),
+                                      ctypes.POINTER(md_stats), _VP]),
+    ("md_cluster_sampling", ctypes.c_int, [ctypes.POINTER(md_grid), ctypes.c_int64, c_int64_p, c_double_p,
+                                           ctypes.c_double, c_int64_p, c_int64_p, c_double_p]),
+    ("md_fermi_level_poles", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(md_nodes), _VP,
+                                            ctypes.POINTER(md_solver_opts), ctypes.c_double, ctypes.c_double,
+                                            c_double_p, c_double_p, c_int32_p, _VP]),
     ("md_density_adjoint", ctypes.c_int, [_VP, ctypes.POINTER(md_poles), ctypes.POINTER(md_nodes),
                                           ctypes.POINTER(md_solver_opts), _VP, _VP, _VP, _VP, _VP,
                                           ctypes.POINTER(md_stats), _VP]),
@@ -118,6 +137,7 @@ SIGNATURES = [
                                        ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP]),
     ("md_fermi_level", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_double,
                                       ctypes.c_double, c_double_p, c_double_p, _VP]),
+    ("md_fma_rate", ctypes.c_int, [ctypes.c_int32, _VP, c_double_p]),
     ("md_last_error", ctypes.c_char_p, []),
     ("md_version", ctypes.c_char_p, []),
 ]

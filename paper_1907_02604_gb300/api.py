@@ -45,6 +45,14 @@ def fd_weights(order: int) -> np.ndarray:
     return out
 
 
+def fma_rate(precision: str = "fp64", stream=None) -> float:
+    """Measured FMA throughput of the device in TFLOP/s (md_fma_rate)."""
+    prec = {"fp64": _lib.MD_PREC_FP64, "fp32": _lib.MD_PREC_MIXED}[precision]
+    out = ctypes.c_double()
+    check(load().md_fma_rate(prec, _stream_handle(stream), ctypes.byref(out)), "md_fma_rate")
+    return out.value
+
+
 def make_poles(kT: float, mu: float, emin: float, emax: float, P: int):
     """Poles and weights (complex128 arrays) of the rational Fermi
     approximation (host code, no GPU)."""
@@ -64,12 +72,16 @@ class SolverOptions:
     timeout_s: float = 0.0
     block: int = 0
     ctas_per_sm: int = 0
-    kernel: str = "auto"           # "auto", "generic" or "zmarch" (the last two need block > 0)
+    # "auto" (autotuned), "generic" or "zmarch" (both need block > 0), or
+    # "cluster": Krylov vectors in shared memory, one thread-block cluster per
+    # system (mixed precision); there ctas_per_sm is the CTAs per cluster
+    # (0 = the fewest whose slabs fit) and block the threads per CTA (0 = auto)
+    kernel: str = "auto"
     method: str = "cocg"           # "cocg" (one solve per pole) or "shifted" (one per node)
 
     def to_c(self) -> _lib.md_solver_opts:
         prec = {"fp64": _lib.MD_PREC_FP64, "mixed": _lib.MD_PREC_MIXED}[self.precision]
-        kern = {"auto": 0, "generic": 1, "zmarch": 2}[self.kernel]
+        kern = {"auto": 0, "generic": 1, "zmarch": 2, "cluster": 3}[self.kernel]
         meth = {"cocg": 0, "shifted": 1}[self.method]
         return _lib.md_solver_opts(self.tol, self.maxit, prec, self.reliable_every,
                                    self.reliable_delta, self.timeout_s, self.block, self.ctas_per_sm,
@@ -287,18 +299,97 @@ def density(ham: Hamiltonian, z, w, nodes, halfwidth, opts: SolverOptions = None
     return rho, e, d
 
 
-def energy(ham: Hamiltonian, z, w, nodes, halfwidth, opts: SolverOptions = None, stream=None):
-    """Band energy per node (device tensor) and its sum (float)."""
+def energy(ham: Hamiltonian, z, w, nodes, halfwidth, opts: SolverOptions = None, node_weight=None,
+           stream=None):
+    """Band energy per node (device tensor) and its node-weighted sum (float;
+    node_weight: float64 CUDA tensor of n_nodes, or None for weight 1)."""
     opts = opts or SolverOptions()
     pa, na = _PoleArgs(z, w), _NodeArgs(nodes, halfwidth)
+    nu = None if node_weight is None else _cuda_f64(node_weight, na.n, "node_weight")
     e = torch.empty(na.n, dtype=torch.float64, device="cuda")
     eb = ctypes.c_double()
     st = _lib.md_stats()
     copts = opts.to_c()
-    check(load().md_energy(ham.handle, ctypes.byref(pa.c), ctypes.byref(na.c), ctypes.byref(copts),
+    check(load().md_energy(ham.handle, ctypes.byref(pa.c), ctypes.byref(na.c),
+                           None if nu is None else ctypes.c_void_p(nu.data_ptr()), ctypes.byref(copts),
                            ctypes.c_void_p(e.data_ptr()), ctypes.byref(eb), ctypes.byref(st),
                            _stream_handle(stream)), "md_energy")
     return e, eb.value, st.as_dict()
+
+
+def make_entropy_weights(kT: float, mu: float, emin: float, emax: float, P: int):
+    """Weights (complex128) of the entropy function on the poles make_poles
+    returns for the same arguments (host code, no GPU)."""
+    w = np.zeros(2 * P)
+    check(load().md_make_entropy_weights(kT, mu, emin, emax, P, _dptr(w)), "md_make_entropy_weights")
+    return w[0::2] + 1j * w[1::2]
+
+
+def free_energy(ham: Hamiltonian, z, w, w_entropy, kT: float, nodes, halfwidth, opts: SolverOptions = None,
+                node_weight=None, stream=None, strict=True):
+    """rho_j, e_j and s_j (device tensors) and the node-weighted totals
+    {n_electrons, e_band, ts, free_energy} (md_free_energy).  w_entropy from
+    make_entropy_weights, or None (no entropy term: s is None, ts = 0)."""
+    opts = opts or SolverOptions()
+    pa, na = _PoleArgs(z, w), _NodeArgs(nodes, halfwidth)
+    nu = None if node_weight is None else _cuda_f64(node_weight, na.n, "node_weight")
+    ws = None
+    if w_entropy is not None:
+        w_entropy = np.asarray(w_entropy, dtype=np.complex128)
+        if w_entropy.shape != (pa.P,):
+            raise ValueError("w_entropy must have one weight per pole")
+        ws = np.empty(2 * pa.P)
+        ws[0::2], ws[1::2] = w_entropy.real, w_entropy.imag
+    rho = torch.empty(na.n, dtype=torch.float64, device="cuda")
+    e = torch.empty(na.n, dtype=torch.float64, device="cuda")
+    s = torch.empty(na.n, dtype=torch.float64, device="cuda") if ws is not None else None
+    terms = _lib.md_free_energy_terms()
+    st = _lib.md_stats()
+    copts = opts.to_c()
+    vp = lambda t: None if t is None or t.numel() == 0 else ctypes.c_void_p(t.data_ptr())
+    status = load().md_free_energy(ham.handle, ctypes.byref(pa.c), None if ws is None else _dptr(ws), float(kT),
+                                   ctypes.byref(na.c), vp(nu), ctypes.byref(copts), vp(rho), vp(e), vp(s),
+                                   ctypes.byref(terms), ctypes.byref(st), _stream_handle(stream))
+    check(status, "md_free_energy", allow=() if strict else _SOFT)
+    d = st.as_dict()
+    d["status"] = _lib.STATUS_NAMES[status]
+    return rho, e, s, terms.as_dict(), d
+
+
+def cluster_sampling(shape, spacing, periodic, esp, n_q, radius: float):
+    """Nodes (int64) and weights (float64) of the cluster-sampled energy of
+    Section 3 (md_cluster_sampling; host code, no GPU)."""
+    g = _lib.md_grid((ctypes.c_int32 * 3)(*[int(n) for n in shape]),
+                     (ctypes.c_double * 3)(*[float(h) for h in spacing]),
+                     (ctypes.c_int32 * 3)(*[1 if p else 0 for p in periodic]), 2)
+    esp = np.ascontiguousarray(esp, dtype=np.int64)
+    n_q = np.ascontiguousarray(n_q, dtype=np.float64)
+    n = ctypes.c_int64(0)
+    lib = load()
+    check(lib.md_cluster_sampling(ctypes.byref(g), len(esp), esp.ctypes.data_as(_lib.c_int64_p), _dptr(n_q),
+                                  float(radius), ctypes.byref(n), None, None), "md_cluster_sampling")
+    nodes = np.zeros(n.value, np.int64)
+    nu = np.zeros(n.value, np.float64)
+    check(lib.md_cluster_sampling(ctypes.byref(g), len(esp), esp.ctypes.data_as(_lib.c_int64_p), _dptr(n_q),
+                                  float(radius), ctypes.byref(n), nodes.ctypes.data_as(_lib.c_int64_p),
+                                  _dptr(nu)), "md_cluster_sampling")
+    return nodes, nu
+
+
+def fermi_level_poles(ham: Hamiltonian, kT: float, P: int, nodes, halfwidth, n_electrons: float,
+                      opts: SolverOptions = None, node_weight=None, mu_tol: float = 0.0, stream=None):
+    """(mu, N(mu), counts made) with N(mu) = dV sum nu_j rho_j(mu) = n_electrons
+    for the pole form (md_fermi_level_poles)."""
+    opts = opts or SolverOptions()
+    na = _NodeArgs(nodes, halfwidth)
+    nu = None if node_weight is None else _cuda_f64(node_weight, na.n, "node_weight")
+    mu, cnt, ev = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    copts = opts.to_c()
+    check(load().md_fermi_level_poles(ham.handle, float(kT), int(P), ctypes.byref(na.c),
+                                      None if nu is None else ctypes.c_void_p(nu.data_ptr()), ctypes.byref(copts),
+                                      float(n_electrons), float(mu_tol), ctypes.byref(mu), ctypes.byref(cnt),
+                                      ctypes.byref(ev), _stream_handle(stream)), "md_fermi_level_poles")
+    return mu.value, cnt.value, ev.value
 
 
 def density_fused_adjoint(ham: Hamiltonian, z, w, nodes, halfwidth, dL_drho: torch.Tensor = None,

@@ -116,6 +116,37 @@ struct Regions {
     bool any_ring = false;
 };
 
+// Region of node g with half-width s (the cube of side 2s+1 around it,
+// wrapped on periodic axes, the whole axis as a ring where 2s+1 >= n):
+// descriptor and point count; MD_ERR_INVALID for a bad node or region.
+md_status build_node_desc(const Ham& H, long long g, int s, NodeDesc& d, long long& pts) {
+    if (g < 0 || g >= H.N) return set_error(MD_ERR_INVALID, "node index out of range");
+    if (s < 0) return set_error(MD_ERR_INVALID, "negative region half-width");
+    const int c[3] = {(int)(g % H.n[0]), (int)((g / H.n[0]) % H.n[1]), (int)(g / ((long long)H.n[0] * H.n[1]))};
+    d.ring = 0;
+    int srcc[3];
+    pts = 1;
+    for (int ax = 0; ax < 3; ++ax) {
+        const long long m = 2LL * s + 1;
+        if (H.periodic[ax] && m >= H.n[ax]) {
+            d.dims[ax] = H.n[ax];
+            d.lo[ax] = 0;
+            d.ring |= 1 << ax;
+            srcc[ax] = c[ax];
+        } else {
+            if (!H.periodic[ax] && (c[ax] - s < 0 || c[ax] + s >= H.n[ax]))
+                return set_error(MD_ERR_INVALID, "region leaves a non-periodic grid axis");
+            d.dims[ax] = (int)m;
+            d.lo[ax] = c[ax] - s;
+            srcc[ax] = s;
+        }
+        pts *= d.dims[ax];
+    }
+    if (pts > (1LL << 30)) return set_error(MD_ERR_INVALID, "region too large");
+    d.src = srcc[0] + d.dims[0] * (srcc[1] + d.dims[1] * srcc[2]);
+    return MD_OK;
+}
+
 md_status make_regions(const Ham& H, const md_nodes* nodes, Regions& R) {
     if (!nodes || nodes->n_nodes < 0 || (nodes->n_nodes > 0 && (!nodes->node || !nodes->halfwidth)))
         return set_error(MD_ERR_INVALID, "nodes: null arrays or negative count");
@@ -125,36 +156,12 @@ md_status make_regions(const Ham& H, const md_nodes* nodes, Regions& R) {
     R.total = 0;
     R.n_max = 0;
     for (long long j = 0; j < nn; ++j) {
-        const long long g = nodes->node[j];
-        const int s = nodes->halfwidth[j];
-        if (g < 0 || g >= H.N) return set_error(MD_ERR_INVALID, "node index out of range");
-        if (s < 0) return set_error(MD_ERR_INVALID, "negative region half-width");
-        const int c[3] = {(int)(g % H.n[0]), (int)((g / H.n[0]) % H.n[1]),
-                          (int)(g / ((long long)H.n[0] * H.n[1]))};
         NodeDesc& d = R.desc[j];
-        d.ring = 0;
-        int srcc[3];
-        long long pts = 1;
-        for (int ax = 0; ax < 3; ++ax) {
-            const long long m = 2LL * s + 1;
-            if (H.periodic[ax] && m >= H.n[ax]) {
-                d.dims[ax] = H.n[ax];
-                d.lo[ax] = 0;
-                d.ring |= 1 << ax;
-                srcc[ax] = c[ax];
-            } else {
-                if (!H.periodic[ax] && (c[ax] - s < 0 || c[ax] + s >= H.n[ax]))
-                    return set_error(MD_ERR_INVALID, "region leaves a non-periodic grid axis");
-                d.dims[ax] = (int)m;
-                d.lo[ax] = c[ax] - s;
-                srcc[ax] = s;
-            }
-            pts *= d.dims[ax];
-        }
-        if (pts > (1LL << 30)) return set_error(MD_ERR_INVALID, "region too large");
+        long long pts = 0;
+        const md_status st = build_node_desc(H, nodes->node[j], nodes->halfwidth[j], d, pts);
+        if (st != MD_OK) return st;
         for (int ax = 0; ax < 3; ++ax) R.max_dim[ax] = std::max(R.max_dim[ax], d.dims[ax]);
         if (d.ring) R.any_ring = true;
-        d.src = srcc[0] + d.dims[0] * (srcc[1] + d.dims[1] * srcc[2]);
         R.points[j] = pts;
         R.total += pts;
         R.n_max = std::max(R.n_max, pts);
@@ -191,7 +198,7 @@ md_status check_opts(const md_solver_opts* o) {
         return set_error(MD_ERR_INVALID, "opts: unknown precision");
     if (o->block != 0 && (o->block < 64 || o->block > 1024 || o->block % 32))
         return set_error(MD_ERR_INVALID, "opts: block must be a multiple of 32 in [64, 1024]");
-    if (o->kernel < 0 || o->kernel > 2) return set_error(MD_ERR_INVALID, "opts: kernel must be 0, 1 or 2");
+    if (o->kernel < 0 || o->kernel > 3) return set_error(MD_ERR_INVALID, "opts: kernel must be 0, 1, 2 or 3");
     if (o->method < 0 || o->method > 1) return set_error(MD_ERR_INVALID, "opts: method must be 0 or 1");
     return MD_OK;
 }
@@ -220,6 +227,9 @@ struct md_plan {
     long long n_sys = 0;
     int grid = 0, block = 0, per_sm = 1;
     int variant = 0;                   // 0 generic kernel, K > 0: z-march kernel with K columns per thread
+    int cluster = 0;                   // > 0: cluster kernel with this many CTAs per system
+    size_t cl_smem = 0;                // dynamic shared memory of the cluster kernel
+    int cl_block = 0;                  // its threads per CTA
     bool multishift = false;           // one shifted-COCG work item per node
     size_t smem = 0;                   // dynamic shared memory of the z-march kernel
     std::vector<long long> points;     // region points per node
@@ -274,13 +284,77 @@ void plan_free(md_plan* pl) {
     delete pl;
 }
 
+// A launch shape.  Generic and z-march kernels: per_sm CTAs per SM.  Cluster
+// kernel (cluster > 0): per_sm = resident clusters on the device.
 struct Shape {
     int variant, block, per_sm;
+    int cluster = 0;
 };
 
+int grid_of(const Shape& sh, int n_sm, long long n_work) {
+    if (sh.cluster > 0) return (int)std::min<long long>(sh.per_sm, n_work) * sh.cluster;
+    return (int)std::min<long long>((long long)n_sm * sh.per_sm, n_work);
+}
+
+// Scratch the shape needs: one Krylov slot per CTA, or per cluster.
+size_t scratch_of(const SolveParams& P, const Shape& sh, int grid) {
+    if (sh.cluster > 0)
+        return cl_slot_bytes(P.n_max, sh.cluster, P.cl_slab, P.nonlocal, P.cl_row_cap, P.cl_key_cap) * (size_t)(grid / sh.cluster);
+    return P.slot_bytes * (size_t)grid;
+}
+
 cudaError_t launch_shape(const md_plan* pl, const SolveParams& P, const Shape& sh, int grid, cudaStream_t s) {
+    if (sh.cluster > 0) {
+        SolveParams C = P;
+        C.slot_bytes = cl_slot_bytes(P.n_max, sh.cluster, P.cl_slab, P.nonlocal, P.cl_row_cap, P.cl_key_cap);
+        return launch_cocg_cl(C, sh.cluster, grid, sh.block, pl->cl_smem, s);
+    }
     if (sh.variant > 0) return launch_cocg_zm(P, sh.variant, grid, sh.block, pl->smem, s);
     return launch_cocg(P, pl->precision, grid, sh.block, sh.per_sm, s);
+}
+
+// Cluster-kernel geometry for regions of at most m2 planes of at most
+// `plane` points: among the cluster sizes (<= 8 CTAs, or the given size
+// `force` > 0) whose thickest slab of p and r fits in shared memory, the one
+// that keeps the most SMs busy; the CTA size (a multiple of 32 up to the
+// kernel's limit) with the most threads that wastes at most 6 % more thread
+// slots on one plane's columns than the best; and, with projector windows
+// wx points long (0: no projectors), how many atoms' x tables the leftover
+// shared memory holds (xcap).  Returns false if no cluster size fits.
+bool cl_geometry(int q, int m2, int plane, int dev, int force, int wx, int& csz, int& slab, size_t& smem,
+                 int& block, int& xcap) {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t budget = (size_t)optin > cl_static_smem_bytes() ? (size_t)optin - cl_static_smem_bytes() : 0;
+    // CTA size: the most threads whose column assignment wastes at most 6 %
+    // more thread slots than the best one (more warps hide more latency)
+    double best = 0.0;
+    for (int t = 64; t <= cl_max_threads(); t += 32)
+        best = std::max(best, (double)plane / (double)(((plane + t - 1) / t) * t));
+    block = 64;
+    for (int t = 64; t <= cl_max_threads(); t += 32)
+        if ((double)plane / (double)(((plane + t - 1) / t) * t) >= best - 0.06) block = t;
+    // among the sizes whose slabs fit, the one that keeps the most SMs busy
+    // (clusters are placed within a GPC, so larger clusters strand SMs);
+    // ties go to the smaller cluster (fewer halo planes)
+    csz = 0;
+    long long best_cover = 0;
+    for (int c = force > 0 ? force : 1; c <= (force > 0 ? force : 8); ++c) {
+        const long long sp = (long long)((m2 + c - 1) / c) * plane;
+        if (sp >= (1LL << 30) || cl_smem_bytes((int)sp, 0) > budget) continue;
+        if ((m2 + c - 1) / c > 255) continue;   // the nonlocal row records hold the slab plane in 8 bits
+        const long long cover = (long long)cl_max_clusters(q, c, block, cl_smem_bytes((int)sp, 0)) * c;
+        if (cover > best_cover) {
+            best_cover = cover;
+            csz = c;
+            slab = (int)sp;
+        }
+    }
+    if (csz == 0) return false;
+    const size_t base = cl_smem_bytes(slab, 0);
+    xcap = wx > 0 ? (int)std::min<size_t>(kMaxLocalProjAtoms, (budget - base) / (8 * (size_t)wx)) : 0;
+    smem = cl_smem_bytes(slab, 2 * xcap * wx);
+    return true;
 }
 
 // Candidate launch shapes: the generic kernel at 1024x1 and 512x2 (and, in
@@ -291,6 +365,10 @@ cudaError_t launch_shape(const md_plan* pl, const SolveParams& P, const Shape& s
 std::vector<Shape> candidate_shapes(const md_plan* pl, bool zm_ok, int max_plane) {
     std::vector<Shape> c = {{0, 1024, 1}, {0, 512, 2}};
     if (pl->precision == MD_PREC_MIXED) c.push_back({0, 512, 3});
+    if (pl->cluster > 0) {
+        const int n_cl = cl_max_clusters(pl->P.q, pl->cluster, pl->cl_block, pl->cl_smem);
+        if (n_cl > 0) c.push_back({0, pl->cl_block, n_cl, pl->cluster});
+    }
     if (!zm_ok) return c;
     for (int K = 1; K <= 4; ++K) {
         const int need = (max_plane + K - 1) / K;
@@ -328,7 +406,7 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
     int dev = 0;
     cudaGetDevice(&dev);
     const TuneKey key{pl->precision, pl->P.q, (int)((pl->P.n_max + 4095) / 4096), pl->P.nonlocal,
-                      (cands.size() > 2 ? 1 : 0) + 2 * pl->P.multishift, dev};
+                      (cands.size() > 2 ? 1 : 0) + 2 * pl->P.multishift + 4 * (pl->cluster > 0 ? 1 : 0), dev};
     {
         std::lock_guard<std::mutex> guard(g_tune_mutex);
         for (const auto& e : g_tune_cache)
@@ -338,12 +416,14 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
             }
     }
     const long long nw = pl->P.n_sys;   // work items (systems, or nodes with shifted COCG)
-    int max_per = 1;
-    for (const auto& c : cands) max_per = std::max(max_per, c.per_sm);
+    // systems in flight at once per candidate: one per CTA, or one per cluster
+    long long max_flight = 1;
+    for (const auto& c : cands)
+        max_flight = std::max<long long>(max_flight, c.cluster > 0 ? c.per_sm : (long long)n_sm * c.per_sm);
     // enough systems that every candidate's CTAs each take four in turn, so
     // that the trial's tail (CTAs idle at its end) weighs little, as in a
     // full batch
-    const long long ns = std::min<long long>(nw, 4LL * n_sm * max_per);
+    const long long ns = std::min<long long>(nw, 4LL * max_flight);
     std::vector<SysDesc> all(nw), sample;
     PLAN_TRY(cudaMemcpy(all.data(), pl->d_sys, nw * sizeof(SysDesc), cudaMemcpyDeviceToHost));
     for (long long k = 0; k < ns; ++k) sample.push_back(all[(k * nw) / ns]);
@@ -368,8 +448,8 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
         T.ckpt = nullptr;         // trials never touch the checkpoint
         T.fused_dLdV = nullptr;   // nor the gradient
         T.dm_rows = nullptr;
-        const int grid = (int)std::min<long long>((long long)n_sm * c.per_sm, ns);
-        if (pl->P.slot_bytes * (size_t)grid > scratch_bytes) continue;
+        const int grid = grid_of(c, n_sm, ns);
+        if (scratch_of(pl->P, c, grid) > scratch_bytes) continue;
         // best of two runs (one for a z-march shape already far behind); the
         // counter reset is ordered on the trial stream
         float ms = 0.f;
@@ -406,8 +486,10 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
         if (failed) continue;
         const double rate = ms > 0 ? (double)pit / ms : 0.0;
         if (std::getenv("MD_AUTOTUNE_LOG"))
-            std::fprintf(stderr, "md autotune: variant %d block %d ctas/SM %d: %.3f ms, %.3g point-iterations/s\n",
-                         c.variant, c.block, c.per_sm, ms, rate * 1e3);
+            std::fprintf(stderr,
+                         "md autotune: variant %d cluster %d block %d ctas/SM or clusters %d: %.3f ms, %.3g "
+                         "point-iterations/s\n",
+                         c.variant, c.cluster, c.block, c.per_sm, ms, rate * 1e3);
         if (c.variant > 0 && rate < 0.5 * best) zm_hopeless = true;
         if (rate > best) {
             best = rate;
@@ -487,7 +569,7 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     const bool ms = opts.method == 1;
     if (ms && ckpt) return set_error(MD_ERR_INVALID, "method 1 (shifted COCG) keeps no checkpoint");
     if (ms && Pn > 64) return set_error(MD_ERR_INVALID, "method 1 (shifted COCG) handles at most 64 poles");
-    if (ms && opts.kernel == 2) return set_error(MD_ERR_INVALID, "method 1 runs on the generic kernel");
+    if (ms && opts.kernel >= 2) return set_error(MD_ERR_INVALID, "method 1 runs on the generic kernel");
     if (fused && ms) return set_error(MD_ERR_INVALID, "the fused adjoint needs method 0");
 
     md_plan* pl = new md_plan();
@@ -606,9 +688,28 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     P.zm_m0 = R.max_dim[0];
     P.zm_m1 = R.max_dim[1];
     if (zm_ok) pl->smem = zm_smem_bytes(H.q, R.max_dim[0], R.max_dim[1]);
-    // scratch sized for the widest candidate (3 CTAs per SM)
+    // the cluster kernel: mixed precision, no whole-axis rings, per-pole COCG
+    // (regions with at most 255 points along y: the row records hold the row in 8 bits)
+    P.cl_wx = P.nonlocal ? std::min(2 * (int)std::floor(H.proj_rc / H.h[0]) + 2, kMaxProjWin) : 0;
+    const bool cl_ok = cl_supported(opts.precision, H.q) && !R.any_ring && !ms && R.max_dim[1] <= 255 &&
+                       cl_geometry(H.q, R.max_dim[2], max_plane, dev,
+                                   opts.kernel == 3 && opts.ctas_per_sm > 0 ? std::min(opts.ctas_per_sm, 8) : 0,
+                                   P.cl_wx, pl->cluster, P.cl_slab, pl->cl_smem, pl->cl_block, P.cl_xcap);
+    if (!cl_ok) pl->cluster = 0;
+    if (cl_ok && P.nonlocal) {
+        // row records per CTA: every local atom (at most kMaxLocalProjAtoms) x
+        // its window rows on y x the slab's planes x two x-runs
+        const int win_y = 2 * (int)std::floor(H.proj_rc / H.h[1]) + 2;
+        const int depth = (R.max_dim[2] + pl->cluster - 1) / pl->cluster;
+        P.cl_row_cap = kMaxLocalProjAtoms * std::min(win_y, kMaxProjWin) * depth * 2;
+        P.cl_key_cap = depth * R.max_dim[1];
+    }
+    // scratch sized for the widest candidate (3 CTAs per SM, or one slot per SM for clusters)
     const int max_ctas = (int)std::min<long long>((long long)n_sm * 3, n_work);
-    const size_t need = P.slot_bytes * (size_t)max_ctas;
+    const size_t need = std::max(P.slot_bytes * (size_t)max_ctas,
+                                 cl_ok ? cl_slot_bytes(P.n_max, pl->cluster, P.cl_slab, P.nonlocal, P.cl_row_cap, P.cl_key_cap) *
+                                             (size_t)std::min<long long>(n_sm, n_work)
+                                       : 0);
     if (borrow_scratch) {
         if (need > H.scratch_bytes) {
             if (H.scratch) cudaFree(H.scratch);
@@ -624,7 +725,18 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     P.scratch = (char*)pl->scratch;
 
     Shape shape{0, opts.block > 0 ? opts.block : 512, opts.ctas_per_sm > 0 ? opts.ctas_per_sm : 0};
-    if (opts.block > 0 && opts.kernel == 2) {
+    if (opts.kernel == 3) {   // the cluster kernel, forced
+        if (!cl_ok)
+            return fail(set_error(MD_ERR_INVALID,
+                                  "opts: the cluster kernel needs mixed precision, stencil order <= 8, no "
+                                  "whole-axis rings, method 0 and regions whose slabs fit in shared memory"));
+        const int blk = opts.block > 0 ? opts.block : pl->cl_block;
+        if (blk > cl_max_threads())
+            return fail(set_error(MD_ERR_INVALID, "opts: block exceeds the cluster kernel's thread limit"));
+        const int n_cl = cl_max_clusters(H.q, pl->cluster, blk, pl->cl_smem);
+        if (n_cl <= 0) return fail(set_error(MD_ERR_CUDA, "the cluster kernel cannot be made resident"));
+        shape = Shape{0, blk, n_cl, pl->cluster};
+    } else if (opts.block > 0 && opts.kernel == 2) {
         const int K = (max_plane + opts.block - 1) / opts.block;
         if (!zm_ok || K < 1 || K > 4 || opts.block > zm_max_threads(K))
             return fail(set_error(MD_ERR_INVALID,
@@ -633,23 +745,26 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
         shape.variant = K;
         if (shape.per_sm <= 0) shape.per_sm = 1;
     }
-    if (opts.block <= 0) {
+    if (opts.block <= 0 && opts.kernel != 3) {
         const std::vector<Shape> cands = candidate_shapes(pl, zm_ok, max_plane);
         md_status ts = autotune(pl, n_sm, cands, need, shape);
         if (ts != MD_OK) return fail(ts);
     }
-    if (shape.per_sm <= 0) shape.per_sm = std::max(1, 1024 / shape.block);
-    shape.per_sm = std::min(shape.per_sm, opts.precision == MD_PREC_MIXED && shape.variant == 0 ? 3 : 2);
+    if (shape.cluster == 0) {
+        if (shape.per_sm <= 0) shape.per_sm = std::max(1, 1024 / shape.block);
+        shape.per_sm = std::min(shape.per_sm, opts.precision == MD_PREC_MIXED && shape.variant == 0 ? 3 : 2);
+    }
     pl->variant = shape.variant;
     pl->block = shape.block;
     pl->per_sm = shape.per_sm;
-    pl->grid = (int)std::min<long long>((long long)n_sm * shape.per_sm, n_work);
+    pl->cluster = shape.cluster;
+    pl->grid = grid_of(shape, n_sm, n_work);
 
     // capture [reset counter, solver, accumulation] once; launches replay it
     PTRY(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
     {
         cudaError_t e1 = cudaMemsetAsync(pl->d_counter, 0, sizeof(unsigned int), pl->cap);
-        cudaError_t e2 = launch_shape(pl, P, Shape{pl->variant, pl->block, pl->per_sm}, pl->grid, pl->cap);
+        cudaError_t e2 = launch_shape(pl, P, Shape{pl->variant, pl->block, pl->per_sm, pl->cluster}, pl->grid, pl->cap);
         cudaError_t e3 = launch_accumulate((int)nn, Pn, pl->d_xsrc, pl->d_z, pl->d_w, H.dV, rho_out, e_out, pl->cap);
         cudaError_t e4 = cudaStreamEndCapture(pl->cap, &pl->graph);
         PTRY(e1);
@@ -745,6 +860,224 @@ md_status density_impl(const md_hamiltonian* ham, const md_poles* poles, const m
     return st;
 }
 
+// Fatal statuses end a composite call; NOCONV and BREAKDOWN leave outputs
+// written and are passed on.
+bool fatal(md_status st) { return st != MD_OK && st != MD_ERR_NOCONV && st != MD_ERR_BREAKDOWN; }
+
+// Per-pole solves, then s_j from the entropy weights (when given) and the
+// node-weighted totals (Section 3, Eqs. free_cg and free_cg_sampling; Eq.
+// Fermi:Rho for the count).  Synchronises `stream`.
+md_status free_energy_impl(const md_hamiltonian* ham, const md_poles* poles, const double* w_entropy, double kT,
+                           const md_nodes* nodes, const double* node_weight, const md_solver_opts* opts,
+                           double* rho_out, double* e_out, double* s_out, md_free_energy_terms* terms,
+                           md_stats* stats, cudaStream_t s) {
+    if (!ham || !nodes || !terms) return set_error(MD_ERR_INVALID, "ham, nodes and terms are required");
+    if (s_out && !w_entropy) return set_error(MD_ERR_INVALID, "s_out needs the entropy weights");
+    if (w_entropy && !(kT > 0.0)) return set_error(MD_ERR_INVALID, "the entropy term needs kT > 0");
+    md_status st = check_poles(poles);
+    if (st != MD_OK) return st;
+    if (w_entropy)
+        for (int p = 0; p < 2 * poles->n_poles; ++p)
+            if (!std::isfinite(w_entropy[p])) return set_error(MD_ERR_INVALID, "entropy weights: non-finite value");
+    std::memset(terms, 0, sizeof(*terms));
+    const long long nn = nodes->n_nodes;
+    if (nn < 0) return set_error(MD_ERR_INVALID, "nodes: negative count");
+    if (nn == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return MD_OK;
+    }
+    const Ham& H = ham->h;
+    const int Pn = poles->n_poles;
+    double *d_rho = rho_out, *d_e = e_out, *d_s = s_out, *d_tot = nullptr;
+    double2* d_ws = nullptr;
+    md_plan* pl = nullptr;
+    double h_tot[4] = {0.0, 0.0, 0.0, 0.0};
+    st = MD_OK;
+    MD_TRY_CUDA(cudaMallocAsync((void**)&d_tot, 4 * sizeof(double), s));
+    if (!d_rho) MD_TRY_CUDA(cudaMallocAsync((void**)&d_rho, nn * sizeof(double), s));
+    if (!d_e) MD_TRY_CUDA(cudaMallocAsync((void**)&d_e, nn * sizeof(double), s));
+    if (w_entropy && !d_s) MD_TRY_CUDA(cudaMallocAsync((void**)&d_s, nn * sizeof(double), s));
+    if (w_entropy) {
+        MD_TRY_CUDA(cudaMallocAsync((void**)&d_ws, Pn * sizeof(double2), s));
+        MD_TRY_CUDA(cudaMemcpyAsync(d_ws, w_entropy, Pn * sizeof(double2), cudaMemcpyHostToDevice, s));
+    }
+    st = plan_create(ham, poles, nodes, opts, d_rho, d_e, nullptr, true, s, &pl);
+    if (st != MD_OK) goto done;
+    if ((st = plan_launch(pl, s)) != MD_OK) goto done;
+    st = plan_stats(pl, s, stats);
+    if (fatal(st)) goto done;
+    if (w_entropy) MD_TRY_CUDA(launch_entropy((int)nn, Pn, pl->d_xsrc, d_ws, kT, d_s, s));
+    MD_TRY_CUDA(launch_weighted_totals(nn, d_rho, d_e, w_entropy ? d_s : nullptr, node_weight, H.dV, d_tot, s));
+    MD_TRY_CUDA(cudaMemcpyAsync(h_tot, d_tot, sizeof(h_tot), cudaMemcpyDeviceToHost, s));
+    MD_TRY_CUDA(cudaStreamSynchronize(s));
+    terms->n_electrons = h_tot[0];
+    terms->e_band = h_tot[1];
+    terms->ts = h_tot[2];
+    terms->free_energy = h_tot[3];
+done:
+    if (pl) plan_free(pl);
+    if (!rho_out && d_rho) cudaFreeAsync(d_rho, s);
+    if (!e_out && d_e) cudaFreeAsync(d_e, s);
+    if (!s_out && d_s) cudaFreeAsync(d_s, s);
+    if (d_ws) cudaFreeAsync(d_ws, s);
+    if (d_tot) cudaFreeAsync(d_tot, s);
+    return st;
+}
+
+// Cluster sampling of Section 3 (Eqs. free_cg, free_cg_sampling): C_q = the
+// grid points within `radius` of ESP q (minimum image on periodic axes;
+// inside the grid on open ones), N_q = |C_q|; every p in C_q carries
+// n_q / N_q, weights of a point in several clusters summed; points ascending.
+md_status cluster_sampling(const md_grid* g, int64_t n_esp, const int64_t* esp, const double* n_q, double radius,
+                           int64_t* n_out, int64_t* node_out, double* weight_out) {
+    if (!g || !n_out) return set_error(MD_ERR_INVALID, "grid and n_out are required");
+    if (n_esp < 0 || (n_esp > 0 && (!esp || !n_q))) return set_error(MD_ERR_INVALID, "esp and n_q are required");
+    if (!(radius >= 0.0) || !std::isfinite(radius)) return set_error(MD_ERR_INVALID, "radius must be finite, >= 0");
+    long long N = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (g->n[d] < 1 || !(g->h[d] > 0.0)) return set_error(MD_ERR_INVALID, "grid: need n >= 1 and h > 0");
+        N *= g->n[d];
+    }
+    std::vector<std::pair<long long, double>> acc;
+    std::vector<long long> pts;
+    for (long long q = 0; q < n_esp; ++q) {
+        if (esp[q] < 0 || esp[q] >= N) return set_error(MD_ERR_INVALID, "ESP index out of range");
+        if (!std::isfinite(n_q[q])) return set_error(MD_ERR_INVALID, "n_q: non-finite value");
+        const long long c[3] = {esp[q] % g->n[0], (esp[q] / g->n[0]) % g->n[1], esp[q] / ((long long)g->n[0] * g->n[1])};
+        int reach[3];
+        for (int d = 0; d < 3; ++d) reach[d] = (int)std::floor(radius / g->h[d]) + 1;
+        pts.clear();
+        for (int oz = -reach[2]; oz <= reach[2]; ++oz)
+            for (int oy = -reach[1]; oy <= reach[1]; ++oy)
+                for (int ox = -reach[0]; ox <= reach[0]; ++ox) {
+                    const int o[3] = {ox, oy, oz};
+                    double r2 = 0.0;
+                    for (int d = 0; d < 3; ++d) r2 += (o[d] * g->h[d]) * (o[d] * g->h[d]);
+                    if (r2 > radius * radius) continue;
+                    long long p[3];
+                    bool ok = true;
+                    for (int d = 0; d < 3; ++d) {
+                        p[d] = c[d] + o[d];
+                        if (g->periodic[d]) {
+                            p[d] %= g->n[d];
+                            if (p[d] < 0) p[d] += g->n[d];
+                        } else if (p[d] < 0 || p[d] >= g->n[d]) {
+                            ok = false;
+                        }
+                    }
+                    if (ok) pts.push_back(p[0] + (long long)g->n[0] * (p[1] + (long long)g->n[1] * p[2]));
+                }
+        std::sort(pts.begin(), pts.end());
+        pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
+        for (long long p : pts) acc.emplace_back(p, n_q[q] / (double)pts.size());
+    }
+    std::stable_sort(acc.begin(), acc.end(),
+                     [](const std::pair<long long, double>& a, const std::pair<long long, double>& b) {
+                         return a.first < b.first;
+                     });
+    std::vector<std::pair<long long, double>> merged;
+    for (const auto& e : acc) {
+        if (!merged.empty() && merged.back().first == e.first) merged.back().second += e.second;
+        else merged.push_back(e);
+    }
+    const long long cap = *n_out;
+    *n_out = (int64_t)merged.size();
+    if (!node_out && !weight_out) return MD_OK;
+    if (cap < (long long)merged.size())
+        return set_error(MD_ERR_INVALID, "md_cluster_sampling: output capacity below the point count");
+    for (size_t k = 0; k < merged.size(); ++k) {
+        if (node_out) node_out[k] = merged[k].first;
+        if (weight_out) weight_out[k] = merged[k].second;
+    }
+    return MD_OK;
+}
+
+// Fermi level of the pole form: mu with N(mu) = dV sum_j nu_j rho_j(mu) =
+// n_electrons (Eq. Fermi:Rho with g -> r), each N(mu) from the same plan
+// relaunched with the poles rebuilt at mu on the spectral interval
+// (Illinois variant of regula falsi, Dowell & Jarratt, BIT 11 (1971)).
+md_status fermi_level_poles(const md_hamiltonian* ham, double kT, int P, const md_nodes* nodes,
+                            const double* node_weight, const md_solver_opts* opts, double n_electrons,
+                            double mu_tol, double* mu_out, double* count_out, int32_t* evals_out, cudaStream_t s) {
+    if (!ham || !nodes || !mu_out) return set_error(MD_ERR_INVALID, "ham, nodes and mu_out are required");
+    if (!(kT > 0.0) || P < 2 || P % 2) return set_error(MD_ERR_INVALID, "need kT > 0 and an even P >= 2");
+    if (!(n_electrons >= 0.0) || !std::isfinite(n_electrons))
+        return set_error(MD_ERR_INVALID, "n_electrons must be finite and >= 0");
+    if (!(mu_tol >= 0.0)) return set_error(MD_ERR_INVALID, "mu_tol must be >= 0");
+    if (mu_tol == 0.0) mu_tol = 1e-10;
+    const long long nn = nodes->n_nodes;
+    if (nn < 1) return set_error(MD_ERR_INVALID, "need at least one node");
+    Ham& H = const_cast<md_hamiltonian*>(ham)->h;
+    md_status st = MD_OK;
+    if (!H.bounds_valid && (st = compute_bounds(H, s)) != MD_OK) return st;
+    const double emin = H.emin, emax = H.emax;
+    std::vector<double> z(2 * P), w(2 * P);
+    if ((st = make_poles(kT, 0.5 * (emin + emax), emin, emax, P, z.data(), w.data())) != MD_OK) return st;
+    md_poles pz{P, z.data(), w.data()};
+    double *d_rho = nullptr, *d_tot = nullptr;
+    md_plan* pl = nullptr;
+    int evals = 0;
+    double a = emin, b = emax, fa = 0.0, fb = 0.0, mu = 0.0, fm = 0.0;
+    int side = 0;
+    auto count = [&](double m, double& f) -> md_status {
+        md_status cs = make_poles(kT, m, emin, emax, P, z.data(), w.data());
+        if (cs != MD_OK) return cs;
+        cudaError_t e = cudaMemcpyAsync(pl->d_z, z.data(), P * sizeof(double2), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(pl->d_w, w.data(), P * sizeof(double2), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+        if ((cs = plan_launch(pl, s)) != MD_OK) return cs;
+        cs = plan_stats(pl, s, nullptr);
+        if (fatal(cs)) return cs;
+        double tot[4];
+        e = launch_weighted_totals(nn, d_rho, nullptr, nullptr, node_weight, H.dV, d_tot, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tot, d_tot, sizeof(tot), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+        ++evals;
+        f = tot[0] - n_electrons;
+        return MD_OK;
+    };
+    MD_TRY_CUDA(cudaMallocAsync((void**)&d_rho, nn * sizeof(double), s));
+    MD_TRY_CUDA(cudaMallocAsync((void**)&d_tot, 4 * sizeof(double), s));
+    if ((st = plan_create(ham, &pz, nodes, opts, d_rho, nullptr, nullptr, true, s, &pl)) != MD_OK) goto done;
+    if ((st = count(a, fa)) != MD_OK) goto done;
+    if ((st = count(b, fb)) != MD_OK) goto done;
+    if (fa > 0.0 || fb < 0.0) {
+        st = set_error(MD_ERR_INVALID, "n_electrons lies outside the counts at the ends of the spectral interval");
+        goto done;
+    }
+    mu = fa == 0.0 ? a : b;
+    fm = fa == 0.0 ? fa : fb;
+    while (b - a > mu_tol && evals < 200 && fm != 0.0) {
+        double c = (a * fb - b * fa) / (fb - fa);
+        if (!(c > a && c < b)) c = 0.5 * (a + b);
+        double fc = 0.0;
+        if ((st = count(c, fc)) != MD_OK) goto done;
+        mu = c;
+        fm = fc;
+        if (fc < 0.0) {
+            a = c;
+            fa = fc;
+            if (side == -1) fb *= 0.5;   // the same end moved twice: halve the other's value
+            side = -1;
+        } else {
+            b = c;
+            fb = fc;
+            if (side == +1) fa *= 0.5;
+            side = +1;
+        }
+    }
+    *mu_out = mu;
+    if (count_out) *count_out = fm + n_electrons;
+    if (evals_out) *evals_out = evals;
+done:
+    if (pl) plan_free(pl);
+    if (d_rho) cudaFreeAsync(d_rho, s);
+    if (d_tot) cudaFreeAsync(d_tot, s);
+    cudaStreamSynchronize(s);
+    return st;
+}
+
 }  // namespace
 }  // namespace md
 
@@ -787,7 +1120,6 @@ constexpr size_t kNaTotalBytes = kNaOffSlots + kNaScratchBytes;
 static __device__ __align__(256) unsigned char g_noalloc_area[kNaTotalBytes];
 
 std::mutex g_na_mutex;                       // host buffers below are shared
-char* g_na_dev_ptr[64] = {nullptr};          // device address of the array, per device
 SysDesc g_na_sys[kNaMaxSystems];
 NodeDesc g_na_nodes[kNaMaxNodes];
 long long g_na_points[kNaMaxNodes];
@@ -807,6 +1139,13 @@ extern "C" md_status md_density_noalloc(const md_hamiltonian* ham, const md_pole
     clear_error();
     std::lock_guard<std::mutex> guard(g_na_mutex);
     cudaStream_t stream = (cudaStream_t)stream_;
+    {   // a captured call would replay without the host lock and race on the array
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            return set_error(MD_ERR_INVALID, "md_density_noalloc cannot be captured in a CUDA graph");
+        }
+    }
     md_status st = check_device();
     if (st != MD_OK) return st;
     if (!ham) return set_error(MD_ERR_INVALID, "ham is NULL");
@@ -826,37 +1165,11 @@ extern "C" md_status md_density_noalloc(const md_hamiltonian* ham, const md_pole
         return set_error(MD_ERR_INVALID,
                          "md_density_noalloc: more than MD_NOALLOC_MAX_NODES nodes, "
                          "MD_NOALLOC_MAX_POLES poles or MD_NOALLOC_MAX_SYSTEMS systems");
-    // region descriptors, as md_density builds them, into the static host buffers
+    // region descriptors, built as md_density builds them, into the static host buffers
     long long n_max = 0;
     for (long long j = 0; j < nn; ++j) {
-        const long long g = nodes->node[j];
-        const int s = nodes->halfwidth[j];
-        if (g < 0 || g >= H.N) return set_error(MD_ERR_INVALID, "node index out of range");
-        if (s < 0) return set_error(MD_ERR_INVALID, "negative region half-width");
-        const int c[3] = {(int)(g % H.n[0]), (int)((g / H.n[0]) % H.n[1]),
-                          (int)(g / ((long long)H.n[0] * H.n[1]))};
-        NodeDesc& d = g_na_nodes[j];
-        d.ring = 0;
-        int srcc[3];
-        long long pts = 1;
-        for (int ax = 0; ax < 3; ++ax) {
-            const long long m = 2LL * s + 1;
-            if (H.periodic[ax] && m >= H.n[ax]) {
-                d.dims[ax] = H.n[ax];
-                d.lo[ax] = 0;
-                d.ring |= 1 << ax;
-                srcc[ax] = c[ax];
-            } else {
-                if (!H.periodic[ax] && (c[ax] - s < 0 || c[ax] + s >= H.n[ax]))
-                    return set_error(MD_ERR_INVALID, "region leaves a non-periodic grid axis");
-                d.dims[ax] = (int)m;
-                d.lo[ax] = c[ax] - s;
-                srcc[ax] = s;
-            }
-            pts *= d.dims[ax];
-        }
-        if (pts > (1LL << 30)) return set_error(MD_ERR_INVALID, "region too large");
-        d.src = srcc[0] + d.dims[0] * (srcc[1] + d.dims[1] * srcc[2]);
+        long long pts = 0;
+        if ((st = build_node_desc(H, nodes->node[j], nodes->halfwidth[j], g_na_nodes[j], pts)) != MD_OK) return st;
         g_na_points[j] = pts;
         n_max = std::max(n_max, pts);
     }
@@ -869,17 +1182,14 @@ extern "C" md_status md_density_noalloc(const md_hamiltonian* ham, const md_pole
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= 64) return set_error(MD_ERR_CUDA, "device ordinal beyond 63");
-    // set-up, once per device with that device current: the device address
-    // of the static array (its host-side name is only a stand-in)
-    if (!g_na_dev_ptr[dev]) {
-        void* ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_area);
-        if (e != cudaSuccess || !ptr)
-            return set_error(MD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_na_dev_ptr[dev] = (char*)ptr;
-    }
-    char* base = g_na_dev_ptr[dev];
+    // the device address of the static array in the current device's context
+    // (its host-side name is only a stand-in), looked up on every call so
+    // that a reset context never leaves a stale address behind
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_area);
+    if (e != cudaSuccess || !ptr)
+        return set_error(MD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    char* base = (char*)ptr;
     const long long n_sys = nn * Pn;
     for (long long j = 0; j < nn; ++j)
         for (int p = 0; p < Pn; ++p) g_na_sys[j * Pn + p] = SysDesc{(int)j, p};
@@ -906,7 +1216,11 @@ extern "C" md_status md_density_noalloc(const md_hamiltonian* ham, const md_pole
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, poles->w, Pn * sizeof(double2), cudaMemcpyHostToDevice, stream);
     // the array keeps the previous call's contents: the work counter must start at zero
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
-    if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(stream);   // copies already queued finish before the lock is released
+        cudaGetLastError();
+        return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    }
 
     SolveParams P;
     std::memset(&P, 0, sizeof(P));
@@ -969,7 +1283,13 @@ extern "C" md_status md_density_noalloc(const md_hamiltonian* ham, const md_pole
     if (e == cudaSuccess) e = cudaMemcpyAsync(g_na_nrel, d_nrel, n_sys * sizeof(int), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g_na_resid, d_resid, n_sys * sizeof(double), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        // whatever was queued must finish before the lock is released: the
+        // next call may run on another stream and would overlap on the array
+        cudaStreamSynchronize(stream);
+        cudaGetLastError();
+        return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    }
     md_stats sst;
     std::memset(&sst, 0, sizeof(sst));
     sst.n_systems = n_sys;
@@ -1175,6 +1495,15 @@ extern "C" md_status md_fermi_level(int64_t n_nodes, int32_t K, const double* la
 }
 
 
+md_status md_fma_rate(int32_t precision, void* stream, double* tflops_out) {
+    clear_error();
+    if (!tflops_out || (precision != MD_PREC_FP64 && precision != MD_PREC_MIXED))
+        return set_error(MD_ERR_INVALID, "md_fma_rate: need tflops_out and MD_PREC_FP64 or MD_PREC_MIXED");
+    md_status st = check_device();
+    if (st != MD_OK) return st;
+    return fma_rate_probe(precision, (cudaStream_t)stream, tflops_out);
+}
+
 const char* md_last_error(void) { return md::g_last_error.c_str(); }
 
 const char* md_version(void) { return "macrodft-gb300 0.1 (sm_103a)"; }
@@ -1342,40 +1671,44 @@ md_status md_density(const md_hamiltonian* ham, const md_poles* poles, const md_
 }
 
 md_status md_energy(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,
-                    const md_solver_opts* opts, double* e_out, double* e_band, md_stats* stats,
-                    void* stream) {
+                    const double* node_weight, const md_solver_opts* opts, double* e_out, double* e_band,
+                    md_stats* stats, void* stream) {
     clear_error();
     if (!e_band) return set_error(MD_ERR_INVALID, "e_band is NULL");
-    if (!nodes) return set_error(MD_ERR_INVALID, "nodes is NULL");
-    cudaStream_t s = (cudaStream_t)stream;
-    const long long nn = nodes->n_nodes;
-    double* d_rho = nullptr;
-    double* d_e = e_out;
-    md_status st = MD_OK;
-    std::vector<double> h_e(std::max<long long>(nn, 1));
-    double sum = 0.0;
-    if (nn <= 0) {
-        *e_band = 0.0;
-        return MD_OK;
-    }
-    MD_TRY_CUDA(cudaMallocAsync((void**)&d_rho, nn * sizeof(double), s));
-    if (!d_e) MD_TRY_CUDA(cudaMallocAsync((void**)&d_e, nn * sizeof(double), s));
-    st = density_impl(ham, poles, nodes, opts, d_rho, d_e, nullptr, stats, s);
-    if (st == MD_ERR_INVALID || st == MD_ERR_CUDA || st == MD_ERR_OOM) goto done;
-    {
-        cudaError_t e1 = cudaMemcpyAsync(h_e.data(), d_e, nn * sizeof(double), cudaMemcpyDeviceToHost, s);
-        cudaError_t e2 = cudaStreamSynchronize(s);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) {
-            st = set_error(MD_ERR_CUDA, "copy of node energies failed");
-            goto done;
-        }
-        for (long long j = 0; j < nn; ++j) sum += h_e[j];
-        *e_band = sum;
-    }
-done:
-    cudaFreeAsync(d_rho, s);
-    if (!e_out && d_e) cudaFreeAsync(d_e, s);
+    md_free_energy_terms t;
+    md_status st = free_energy_impl(ham, poles, nullptr, 0.0, nodes, node_weight, opts, nullptr, e_out, nullptr,
+                                    &t, stats, (cudaStream_t)stream);
+    if (st == MD_OK || st == MD_ERR_NOCONV || st == MD_ERR_BREAKDOWN) *e_band = t.e_band;
     return st;
+}
+
+md_status md_free_energy(const md_hamiltonian* ham, const md_poles* poles, const double* w_entropy, double kT,
+                         const md_nodes* nodes, const double* node_weight, const md_solver_opts* opts,
+                         double* rho_out, double* e_out, double* s_out, md_free_energy_terms* terms,
+                         md_stats* stats, void* stream) {
+    clear_error();
+    return free_energy_impl(ham, poles, w_entropy, kT, nodes, node_weight, opts, rho_out, e_out, s_out, terms,
+                            stats, (cudaStream_t)stream);
+}
+
+md_status md_make_entropy_weights(double kT, double mu, double emin, double emax, int32_t P, double* w_out) {
+    clear_error();
+    return make_entropy_weights(kT, mu, emin, emax, P, w_out);
+}
+
+md_status md_cluster_sampling(const md_grid* grid, int64_t n_esp, const int64_t* esp, const double* n_q,
+                              double radius, int64_t* n_out, int64_t* node_out, double* weight_out) {
+    clear_error();
+    return cluster_sampling(grid, n_esp, esp, n_q, radius, n_out, node_out, weight_out);
+}
+
+md_status md_fermi_level_poles(const md_hamiltonian* ham, double kT, int32_t P, const md_nodes* nodes,
+                               const double* node_weight, const md_solver_opts* opts, double n_electrons,
+                               double mu_tol, double* mu_out, double* count_out, int32_t* evals_out,
+                               void* stream) {
+    clear_error();
+    return fermi_level_poles(ham, kT, P, nodes, node_weight, opts, n_electrons, mu_tol, mu_out, count_out,
+                             evals_out, (cudaStream_t)stream);
 }
 
 md_status md_density_adjoint(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <string>
 
+#include <cuda_runtime.h>
 #include <vector_types.h>
 
 #include "../../include/macrodft.h"
@@ -23,6 +24,8 @@ md_status compute_bounds(Ham& H, void* stream);
 md_status set_potential_device(Ham& H, const double* V_in, void* stream);
 md_status make_poles(double kT, double mu, double emin, double emax, int P, double* z_out,
                      double* w_out);
+md_status make_entropy_weights(double kT, double mu, double emin, double emax, int P, double* w_out);
+md_status fma_rate_probe(int precision, cudaStream_t s, double* tflops);
 
 // Device-resident Hamiltonian.
 struct Ham {

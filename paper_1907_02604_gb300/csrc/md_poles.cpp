@@ -20,12 +20,17 @@
 //         z = mu + xi_j,        w = c_j g(xi_j)
 //         z = mu - conj(xi_j),  w = conj(c_j g(-xi_j)),
 //     c_j = h w'(t_j) / (2 pi xi_j), h = 4K/N.
+// The entropy term of Eq. (tot) uses the same nodes with the weights of its
+// own function phi_S (md_make_entropy_weights): the construction needs no
+// more of g than its analyticity off the Matsubara rays, and phi_S has its
+// singularities at the same points.
 // Elliptic functions: K from the arithmetic-geometric mean (A&S 17.6),
 // sn/cn/dn of a real argument from the AGM / descending Landen scheme
 // (A&S 16.4), of a complex argument from the addition formulas
 // (A&S 16.21.1-3).
 #include <cmath>
 #include <complex>
+#include <string>
 
 #include "md_internal.h"
 
@@ -102,16 +107,46 @@ cd fermi_c(cd x, double kT) {
     return 1.0 / (1.0 + std::exp(x / kT));
 }
 
-}  // namespace
+// ln(1 + u) for complex |u| < 1 that stays accurate for tiny |u| (forming
+// 1 + u first would lose the digits of u): the alternating Taylor series to
+// order 16 where |u| < 0.1 (remainder below 0.1^17 / 17), the logarithm of
+// 1 + u elsewhere.
+cd log1p_c(cd u) {
+    if (std::abs(u) < 0.1) {
+        cd acc = 0.0;
+        for (int k = 16; k >= 1; --k) acc = u * ((k % 2 ? 1.0 : -1.0) / k + acc);
+        return acc;
+    }
+    return std::log(1.0 + u);
+}
 
-md_status make_poles(double kT, double mu, double emin, double emax, int P, double* z_out,
-                     double* w_out) {
+// Entropy function of the last term of Eq. (tot), phi_S(x) = -[f ln f +
+// (1-f) ln(1-f)] with f the Fermi-Dirac function, continued analytically off
+// the imaginary rays where its branch points (the Matsubara points) lie.
+// With y = x/kT: phi_S = ln(1 + e^y) - (1 - f) y, evaluated in the
+// half-plane form that keeps the exponential below one in modulus:
+//   Re y > 0:  ln(1 + e^-y) + y e^-y / (1 + e^-y)
+//   else:      ln(1 + e^y)  - y e^y  / (1 + e^y)
+cd entropy_c(cd x, double kT) {
+    const cd y = x / kT;
+    if (y.real() > 0.0) {
+        const cd e = std::exp(-y);
+        return log1p_c(e) + y * e / (1.0 + e);
+    }
+    const cd e = std::exp(y);
+    return log1p_c(e) - y * e / (1.0 + e);
+}
+
+// Trapezoid nodes of the construction above, with the weights of the
+// function phi(x, kT): node j gives the poles mu + xi_j (weight c_j phi(xi_j))
+// and mu - conj(xi_j) (weight conj(c_j phi(-xi_j))).
+md_status contour_poles(cd (*phi)(cd, double), const char* who, double kT, double mu, double emin,
+                        double emax, int P, double* z_out, double* w_out) {
     if (!(kT > 0.0) || !(emax > emin) || !std::isfinite(mu) || !std::isfinite(emin) ||
         !std::isfinite(emax))
-        return set_error(MD_ERR_INVALID, "md_make_poles: need kT > 0, finite mu and emin < emax");
-    if (P < 2 || (P % 2) != 0)
-        return set_error(MD_ERR_INVALID, "md_make_poles: P must be even and >= 2");
-    if (!z_out || !w_out) return set_error(MD_ERR_INVALID, "md_make_poles: null output");
+        return set_error(MD_ERR_INVALID, std::string(who) + ": need kT > 0, finite mu and emin < emax");
+    if (P < 2 || (P % 2) != 0) return set_error(MD_ERR_INVALID, std::string(who) + ": P must be even and >= 2");
+    if (!w_out) return set_error(MD_ERR_INVALID, std::string(who) + ": null output");
     const double dE = std::fmax(std::fabs(emin - mu), std::fabs(emax - mu));
     const double a = (kPi * kT) * (kPi * kT);
     const double lo = a, hi = dE * dE + a;
@@ -133,20 +168,34 @@ md_status make_poles(double kT, double mu, double emin, double emax, int P, doub
         const cd dw = c0 * (2.0 / k) * cn * dn / (den * den);
         const cd xi = std::sqrt(wq - a);
         const cd cj = h * dw / (2.0 * kPi * xi);
-        const cd wa = cj * fermi_c(xi, kT);
-        const cd wb = std::conj(cj * fermi_c(-xi, kT));
-        const cd za = mu + xi;
-        const cd zb = mu - std::conj(xi);
-        z_out[4 * j + 0] = za.real();
-        z_out[4 * j + 1] = za.imag();
-        z_out[4 * j + 2] = zb.real();
-        z_out[4 * j + 3] = zb.imag();
+        const cd wa = cj * phi(xi, kT);
+        const cd wb = std::conj(cj * phi(-xi, kT));
+        if (z_out) {
+            const cd za = mu + xi;
+            const cd zb = mu - std::conj(xi);
+            z_out[4 * j + 0] = za.real();
+            z_out[4 * j + 1] = za.imag();
+            z_out[4 * j + 2] = zb.real();
+            z_out[4 * j + 3] = zb.imag();
+        }
         w_out[4 * j + 0] = wa.real();
         w_out[4 * j + 1] = wa.imag();
         w_out[4 * j + 2] = wb.real();
         w_out[4 * j + 3] = wb.imag();
     }
     return MD_OK;
+}
+
+}  // namespace
+
+md_status make_entropy_weights(double kT, double mu, double emin, double emax, int P, double* w_out) {
+    return contour_poles(entropy_c, "md_make_entropy_weights", kT, mu, emin, emax, P, nullptr, w_out);
+}
+
+md_status make_poles(double kT, double mu, double emin, double emax, int P, double* z_out,
+                     double* w_out) {
+    if (!z_out) return set_error(MD_ERR_INVALID, "md_make_poles: null output");
+    return contour_poles(fermi_c, "md_make_poles", kT, mu, emin, emax, P, z_out, w_out);
 }
 
 }  // namespace md

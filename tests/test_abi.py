@@ -104,3 +104,50 @@ def test_region_size_matches_oracle_regions():
             except ValueError:   # leaves an open axis: the library refuses it too
                 continue
             assert _region_size(ham, node, s) == int(np.prod(reg.dims)), (shape, periodic, node, s)
+
+
+@pytest.mark.parametrize("P", [8, 16, 32, 64])
+@pytest.mark.parametrize("bounds", [(-3.04, 31.97), (0.1, 0.5)])
+def test_make_entropy_weights_matches_oracle(lib, P, bounds):
+    from paper_1907_02604_gb300 import make_entropy_weights
+    from oracle.poles import entropy_weights
+    ws = make_entropy_weights(0.01, 0.2, bounds[0], bounds[1], P)
+    wo = entropy_weights(0.01, 0.2, bounds[0], bounds[1], P)
+    np.testing.assert_allclose(ws, wo, rtol=1e-10, atol=1e-14 * np.abs(wo).max())
+
+
+def test_make_entropy_weights_approximate_the_entropy_function(lib):
+    """The library's weights on the library's poles against the exact
+    entropy function on 10^5 points (the oracle's pinned bound for P = 32)."""
+    from paper_1907_02604_gb300 import make_entropy_weights, make_poles
+    from oracle.poles import entropy_fn
+    z, _ = make_poles(0.01, 0.2, -3.04, 31.97, 32)
+    ws = make_entropy_weights(0.01, 0.2, -3.04, 31.97, 32)
+    e = np.linspace(-3.04, 31.97, 100001)
+    r = np.imag(ws[None, :] / (e[:, None] - z[None, :])).sum(axis=1)
+    assert np.max(np.abs(r - entropy_fn(e - 0.2, 0.01))) < 3e-4
+
+
+@pytest.mark.parametrize("periodic", [(True, True, True), (False, True, False)])
+def test_cluster_sampling_matches_oracle(lib, periodic):
+    from oracle import density as od
+    from paper_1907_02604_gb300 import cluster_sampling
+    from synthetic import make_workload
+    w = make_workload("tiny", shape=(12, 10, 14), periodic=periodic, spacing=(0.5, 0.45, 0.55))
+    rng = np.random.default_rng(7)
+    esp = rng.choice(w.n_grid, 9, replace=False)
+    n_q = rng.integers(1, 30, 9).astype(np.float64)
+    for radius in (0.0, 0.4, 1.3, 2.6):
+        nodes, nu = cluster_sampling(w.shape, w.spacing, w.periodic, esp, n_q, radius)
+        no, nuo = od.cluster_sampling(w, esp, n_q, radius)
+        np.testing.assert_array_equal(nodes, no)
+        np.testing.assert_allclose(nu, nuo, rtol=1e-14)
+
+
+def test_cluster_sampling_rejects_bad_input(lib):
+    from paper_1907_02604_gb300 import cluster_sampling
+    from paper_1907_02604_gb300._lib import MacroDFTError
+    with pytest.raises(MacroDFTError):
+        cluster_sampling((4, 4, 4), (0.5, 0.5, 0.5), (True,) * 3, [64], [1.0], 1.0)
+    with pytest.raises(MacroDFTError):
+        cluster_sampling((4, 4, 4), (0.5, 0.5, 0.5), (True,) * 3, [3], [1.0], -1.0)
