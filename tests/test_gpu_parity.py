@@ -216,3 +216,21 @@ def test_region_halfwidth_sweep_matches_oracle():
         g = gpu_run(w, precision="fp64")
         _, o = oracle_run(w)
         assert rel_err(g["rho"], o.rho) <= FP64_BAR, s
+
+
+@pytest.mark.slow
+def test_bulk_64_nodes_both_precisions_vs_oracle():
+    """The bulk workload's stated check: 64 nodes (1,024 systems, 33^3
+    regions, projectors, P = 16) against the FP64 oracle, in mixed precision
+    (bar 1e-5) and in the FP64 form (bar 1e-6), on the density, the band
+    energy and, per node, the density of every node above 1e-3 of the
+    largest."""
+    from tests.gpu_helpers import rel_err_per_node
+    w = make_workload("bulk_mixed").subset(np.arange(64))
+    _, o = oracle_run(w)
+    for precision, bar in (("mixed", MIXED_BAR), ("fp64", FP64_BAR)):
+        g = gpu_run(w, precision=precision)
+        assert g["stats"]["n_converged"] == w.n_systems, precision
+        assert rel_err(g["rho"], o.rho) <= bar, precision
+        assert rel_err(g["e"], o.e_node) <= bar, precision
+        assert rel_err_per_node(g["rho"], o.rho) <= bar, precision
