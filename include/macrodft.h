@@ -29,9 +29,12 @@
  *     different host threads at once.  Calls on one handle that solve
  *     (md_density, md_energy, md_density_adjoint, md_density_fused_adjoint,
  *     md_density_matrix_rows, md_lssgq_rules) share scratch the handle
- *     caches, so issue them from one thread at a time; each of them ends
- *     synchronised with its stream, so consecutive calls never overlap on
- *     the GPU.  A plan (md_plan_create) owns its own scratch.
+ *     caches, so issue them from one thread at a time.  Each of them but
+ *     the asynchronous form of md_density ends synchronised with its
+ *     stream; the handle orders every solving call after the last
+ *     asynchronous md_density on it (the stream waits on an event, or the
+ *     host does), so consecutive calls never overlap on the GPU, whatever
+ *     streams they use.  A plan (md_plan_create) owns its own scratch.
  */
 #ifndef MACRODFT_H
 #define MACRODFT_H
@@ -214,10 +217,19 @@ md_status md_workspace_destroy(md_workspace* ws);
  *   e_out:   device, n_nodes doubles or NULL, e_j = 2 sum_p Im(w_p(1+z_p x_jp(j))).
  *   ckpt:    NULL, or a workspace made for the same nodes and pole count;
  *            receives every x_jp.
- * Returns MD_OK, or MD_ERR_NOCONV / MD_ERR_BREAKDOWN / MD_ERR_TIMEOUT with
- * the outputs still written (those are known only after synchronising:
- * the call synchronises `stream` when stats != NULL or when it must report
- * them, i.e. always in this version). */
+ *   stats:   NULL, or host; receives the solver statistics.
+ * With stats != NULL the call synchronises `stream` and returns MD_OK, or
+ * MD_ERR_NOCONV / MD_ERR_BREAKDOWN / MD_ERR_TIMEOUT with the outputs still
+ * written.  With stats == NULL it is asynchronous: it enqueues the uploads
+ * (from a pinned staging buffer of the handle, two used in turn), the solver
+ * and the accumulation on `stream`, frees its temporaries stream-ordered
+ * (cudaFreeAsync) and returns MD_OK once they are enqueued; the outputs are
+ * valid after `stream` has been synchronised and per-system failures are not
+ * reported.  The host still waits (a) for the uploads of the call before the
+ * previous one, before it reuses their staging buffer, (b) for the stream,
+ * the first time a node set of its shape is tuned (opts.block == 0), and
+ * (c) for earlier asynchronous calls on the handle, when the handle's
+ * scratch has to grow. */
 md_status md_density(const md_hamiltonian* ham, const md_poles* poles,
                      const md_nodes* nodes, const md_solver_opts* opts,
                      double* rho_out, double* e_out, md_workspace* ckpt,

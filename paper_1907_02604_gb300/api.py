@@ -277,11 +277,14 @@ class Plan:
 
 
 def density(ham: Hamiltonian, z, w, nodes, halfwidth, opts: SolverOptions = None, energy=False,
-            checkpoint: Workspace = None, out=None, stream=None, strict=True):
+            checkpoint: Workspace = None, out=None, stream=None, strict=True, sync=True):
     """rho_j (and e_j) for every node.  Returns (rho, e or None, stats dict).
 
     With strict=False a non-converged or broken-down system does not raise;
-    its status is in the stats."""
+    its status is in the stats.  With sync=False the call only enqueues the
+    work on `stream` (md_density without stats) and returns (rho, e, None):
+    the tensors are valid once the stream has been synchronised, and no
+    per-system status is reported."""
     opts = opts or SolverOptions()
     pa, na = _PoleArgs(z, w), _NodeArgs(nodes, halfwidth)
     rho = out if out is not None else torch.empty(na.n, dtype=torch.float64, device="cuda")
@@ -292,8 +295,10 @@ def density(ham: Hamiltonian, z, w, nodes, halfwidth, opts: SolverOptions = None
                                ctypes.c_void_p(rho.data_ptr()),
                                ctypes.c_void_p(e.data_ptr()) if e is not None else None,
                                checkpoint.handle if checkpoint is not None else None,
-                               ctypes.byref(st), _stream_handle(stream))
+                               ctypes.byref(st) if sync else None, _stream_handle(stream))
     check(status, "md_density", allow=() if strict else _SOFT)
+    if not sync:
+        return rho, e, None
     d = st.as_dict()
     d["status"] = _lib.STATUS_NAMES[status]
     return rho, e, d

@@ -105,7 +105,22 @@ void free_ham(Ham& H) {
                     H.scratch, H.lz_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (Ham::Stage& sg : H.stage) {
+        if (sg.ev) {
+            cudaEventSynchronize(sg.ev);
+            cudaEventDestroy(sg.ev);
+        }
+        if (sg.buf) cudaFreeHost(sg.buf);
+    }
+    if (H.scratch_ev) {
+        cudaEventSynchronize(H.scratch_ev);
+        cudaEventDestroy(H.scratch_ev);
+    }
 }
+
+// Host wait until the last asynchronous md_density call on the handle has
+// finished with its scratch (at once when there was none).
+cudaError_t scratch_idle(Ham& H) { return H.scratch_ev ? cudaEventSynchronize(H.scratch_ev) : cudaSuccess; }
 
 struct Regions {
     std::vector<NodeDesc> desc;
@@ -251,6 +266,8 @@ struct md_plan {
     double* rho_out = nullptr;
     double* e_out = nullptr;
     cudaStream_t cap = nullptr;
+    bool direct = false;               // launched at creation on `dstream`, temporaries freed stream-ordered
+    cudaStream_t dstream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -279,7 +296,10 @@ void plan_free(md_plan* pl) {
     void* ptrs[] = {pl->d_sys, pl->d_nodes, pl->d_ckoff, pl->d_status, pl->d_iters, pl->d_nrel,
                     pl->d_resid, pl->d_xsrc, pl->d_z, pl->d_w, pl->d_counter};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) {
+            if (pl->direct) cudaFreeAsync(p, pl->dstream);
+            else cudaFree(p);
+        }
     if (pl->own_scratch && pl->scratch) cudaFree(pl->scratch);
     delete pl;
 }
@@ -402,7 +422,7 @@ std::vector<TuneEntry> g_tune_cache;
 std::mutex g_tune_mutex;
 
 md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_t scratch_bytes,
-                   Shape& out) {
+                   Shape& out, cudaStream_t wait_first = nullptr) {
     int dev = 0;
     cudaGetDevice(&dev);
     const TuneKey key{pl->precision, pl->P.q, (int)((pl->P.n_max + 4095) / 4096), pl->P.nonlocal,
@@ -415,6 +435,9 @@ md_status autotune(md_plan* pl, int n_sm, const std::vector<Shape>& cands, size_
                 return MD_OK;
             }
     }
+    // a miss runs trials on the plan's stream: the caller's stream must have
+    // finished the uploads they read
+    if (pl->direct) PLAN_TRY(cudaStreamSynchronize(wait_first));
     const long long nw = pl->P.n_sys;   // work items (systems, or nodes with shifted COCG)
     // systems in flight at once per candidate: one per CTA, or one per cluster
     long long max_flight = 1;
@@ -545,10 +568,14 @@ struct FusedArgs {
     const long long* dm_off;
 };
 
+// direct: launch at once on `stream` without a graph and without
+// synchronising it (device temporaries allocated and freed stream-ordered,
+// uploads staged through the handle's pinned buffers); the caller frees the
+// plan right after.  Otherwise the batch is captured as a graph for replay.
 md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md_nodes* nodes,
                       const md_solver_opts* opts_in, double* rho_out, double* e_out, md_workspace* ckpt,
                       bool borrow_scratch, cudaStream_t stream, md_plan** out,
-                      const FusedArgs* fused = nullptr) {
+                      const FusedArgs* fused = nullptr, bool direct = false) {
     *out = nullptr;
     md_status st = check_device();
     if (st != MD_OK) return st;
@@ -583,6 +610,8 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     pl->e_out = e_out;
     pl->own_scratch = !borrow_scratch;
     pl->multishift = ms;
+    pl->direct = direct;
+    pl->dstream = stream;
     std::memset(&pl->P, 0, sizeof(pl->P));
     auto fail = [&](md_status s) {
         plan_free(pl);
@@ -625,31 +654,70 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
         return ca > cb;
     });
     const long long n_work = (long long)sys.size();
-    PTRY(cudaMalloc(&pl->d_sys, n_work * sizeof(SysDesc)));
-    PTRY(cudaMalloc(&pl->d_nodes, nn * sizeof(NodeDesc)));
-    PTRY(cudaMalloc(&pl->d_status, n_sys * sizeof(int)));
-    PTRY(cudaMalloc(&pl->d_iters, n_sys * sizeof(int)));
-    PTRY(cudaMalloc(&pl->d_nrel, n_sys * sizeof(int)));
-    PTRY(cudaMalloc(&pl->d_resid, n_sys * sizeof(double)));
-    PTRY(cudaMalloc(&pl->d_xsrc, n_sys * sizeof(double2)));
-    PTRY(cudaMalloc(&pl->d_z, Pn * sizeof(double2)));
-    PTRY(cudaMalloc(&pl->d_w, Pn * sizeof(double2)));
-    PTRY(cudaMalloc(&pl->d_counter, sizeof(unsigned int)));
-    PTRY(cudaMemcpy(pl->d_sys, sys.data(), n_work * sizeof(SysDesc), cudaMemcpyHostToDevice));
-    PTRY(cudaMemcpy(pl->d_nodes, R.desc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice));
-    PTRY(cudaMemcpy(pl->d_z, poles->z, Pn * sizeof(double2), cudaMemcpyHostToDevice));
-    PTRY(cudaMemcpy(pl->d_w, poles->w, Pn * sizeof(double2), cudaMemcpyHostToDevice));
-    PTRY(cudaMemsetAsync(pl->d_iters, 0, n_sys * sizeof(int), pl->cap));
+    auto dmalloc = [&](auto** p, size_t b) {
+        return direct ? cudaMallocAsync((void**)p, b, stream) : cudaMalloc((void**)p, b);
+    };
+    PTRY(dmalloc(&pl->d_sys, n_work * sizeof(SysDesc)));
+    PTRY(dmalloc(&pl->d_nodes, nn * sizeof(NodeDesc)));
+    PTRY(dmalloc(&pl->d_status, n_sys * sizeof(int)));
+    PTRY(dmalloc(&pl->d_iters, n_sys * sizeof(int)));
+    PTRY(dmalloc(&pl->d_nrel, n_sys * sizeof(int)));
+    PTRY(dmalloc(&pl->d_resid, n_sys * sizeof(double)));
+    PTRY(dmalloc(&pl->d_xsrc, n_sys * sizeof(double2)));
+    PTRY(dmalloc(&pl->d_z, Pn * sizeof(double2)));
+    PTRY(dmalloc(&pl->d_w, Pn * sizeof(double2)));
+    PTRY(dmalloc(&pl->d_counter, sizeof(unsigned int)));
+    std::vector<long long> ckoff;
     if (ckpt) {
-        std::vector<long long> ckoff(n_sys);
+        ckoff.resize(n_sys);
         for (long long j = 0; j < nn; ++j)
             for (int p = 0; p < Pn; ++p) ckoff[j * Pn + p] = Pn * ckpt->node_off[j] + p * R.points[j];
-        PTRY(cudaMalloc(&pl->d_ckoff, n_sys * sizeof(long long)));
-        PTRY(cudaMemcpy(pl->d_ckoff, ckoff.data(), n_sys * sizeof(long long), cudaMemcpyHostToDevice));
+        PTRY(dmalloc(&pl->d_ckoff, n_sys * sizeof(long long)));
     }
-    // the copies above run on the legacy stream; the trials and the capture
-    // below run on the plan's own (non-blocking) stream
-    PTRY(cudaStreamSynchronize(cudaStreamLegacy));
+    if (direct) {
+        // uploads from the handle's pinned staging buffer (a pageable source
+        // would make the copy wait for the stream's earlier work); two
+        // buffers in turn, each reused once its previous uploads are done
+        Ham::Stage& sg = H.stage[H.stage_next];
+        H.stage_next ^= 1;
+        auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+        const size_t o_nodes = up(n_work * sizeof(SysDesc)), o_z = o_nodes + up(nn * sizeof(NodeDesc));
+        const size_t o_w = o_z + up(Pn * sizeof(double2)), o_ck = o_w + up(Pn * sizeof(double2));
+        const size_t need_h = o_ck + (ckpt ? n_sys * sizeof(long long) : 0);
+        if (sg.ev) PTRY(cudaEventSynchronize(sg.ev));
+        else PTRY(cudaEventCreateWithFlags(&sg.ev, cudaEventDisableTiming));
+        if (need_h > sg.bytes) {
+            if (sg.buf) cudaFreeHost(sg.buf);
+            sg.buf = nullptr;
+            sg.bytes = 0;
+            PTRY(cudaMallocHost(&sg.buf, need_h));
+            sg.bytes = need_h;
+        }
+        char* hb = (char*)sg.buf;
+        std::memcpy(hb, sys.data(), n_work * sizeof(SysDesc));
+        std::memcpy(hb + o_nodes, R.desc.data(), nn * sizeof(NodeDesc));
+        std::memcpy(hb + o_z, poles->z, Pn * sizeof(double2));
+        std::memcpy(hb + o_w, poles->w, Pn * sizeof(double2));
+        if (ckpt) std::memcpy(hb + o_ck, ckoff.data(), n_sys * sizeof(long long));
+        PTRY(cudaMemcpyAsync(pl->d_sys, hb, n_work * sizeof(SysDesc), cudaMemcpyHostToDevice, stream));
+        PTRY(cudaMemcpyAsync(pl->d_nodes, hb + o_nodes, nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, stream));
+        PTRY(cudaMemcpyAsync(pl->d_z, hb + o_z, Pn * sizeof(double2), cudaMemcpyHostToDevice, stream));
+        PTRY(cudaMemcpyAsync(pl->d_w, hb + o_w, Pn * sizeof(double2), cudaMemcpyHostToDevice, stream));
+        if (ckpt)
+            PTRY(cudaMemcpyAsync(pl->d_ckoff, hb + o_ck, n_sys * sizeof(long long), cudaMemcpyHostToDevice, stream));
+        PTRY(cudaEventRecord(sg.ev, stream));
+        PTRY(cudaMemsetAsync(pl->d_iters, 0, n_sys * sizeof(int), stream));
+    } else {
+        PTRY(cudaMemcpy(pl->d_sys, sys.data(), n_work * sizeof(SysDesc), cudaMemcpyHostToDevice));
+        PTRY(cudaMemcpy(pl->d_nodes, R.desc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice));
+        PTRY(cudaMemcpy(pl->d_z, poles->z, Pn * sizeof(double2), cudaMemcpyHostToDevice));
+        PTRY(cudaMemcpy(pl->d_w, poles->w, Pn * sizeof(double2), cudaMemcpyHostToDevice));
+        PTRY(cudaMemsetAsync(pl->d_iters, 0, n_sys * sizeof(int), pl->cap));
+        if (ckpt) PTRY(cudaMemcpy(pl->d_ckoff, ckoff.data(), n_sys * sizeof(long long), cudaMemcpyHostToDevice));
+        // the copies above run on the legacy stream; the trials and the capture
+        // below run on the plan's own (non-blocking) stream
+        PTRY(cudaStreamSynchronize(cudaStreamLegacy));
+    }
 
     SolveParams& P = pl->P;
     fill_operator(P, H);
@@ -711,6 +779,11 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
                                              (size_t)std::min<long long>(n_sm, n_work)
                                        : 0);
     if (borrow_scratch) {
+        // an asynchronous call may still use the scratch: a direct plan
+        // orders its stream after it, any other waits on the host (its
+        // trials and its graph run on other streams)
+        if (direct && H.scratch_ev) PTRY(cudaStreamWaitEvent(stream, H.scratch_ev, 0));
+        if (!direct || need > H.scratch_bytes) PTRY(scratch_idle(H));
         if (need > H.scratch_bytes) {
             if (H.scratch) cudaFree(H.scratch);
             H.scratch = nullptr;
@@ -747,7 +820,7 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     }
     if (opts.block <= 0 && opts.kernel != 3) {
         const std::vector<Shape> cands = candidate_shapes(pl, zm_ok, max_plane);
-        md_status ts = autotune(pl, n_sm, cands, need, shape);
+        md_status ts = autotune(pl, n_sm, cands, need, shape, stream);
         if (ts != MD_OK) return fail(ts);
     }
     if (shape.cluster == 0) {
@@ -760,6 +833,16 @@ md_status plan_create(const md_hamiltonian* ham, const md_poles* poles, const md
     pl->cluster = shape.cluster;
     pl->grid = grid_of(shape, n_sm, n_work);
 
+    if (direct) {   // [reset counter, solver, accumulation] on the caller's stream, now
+        PTRY(cudaMemsetAsync(pl->d_counter, 0, sizeof(unsigned int), stream));
+        PTRY(launch_shape(pl, P, Shape{pl->variant, pl->block, pl->per_sm, pl->cluster}, pl->grid, stream));
+        PTRY(launch_accumulate((int)nn, Pn, pl->d_xsrc, pl->d_z, pl->d_w, H.dV, rho_out, e_out, stream));
+        if (!H.scratch_ev) PTRY(cudaEventCreateWithFlags(&H.scratch_ev, cudaEventDisableTiming));
+        PTRY(cudaEventRecord(H.scratch_ev, stream));
+        pl->launched = true;
+        *out = pl;
+        return MD_OK;
+    }
     // capture [reset counter, solver, accumulation] once; launches replay it
     PTRY(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
     {
@@ -847,6 +930,11 @@ md_status density_impl(const md_hamiltonian* ham, const md_poles* poles, const m
                        const md_solver_opts* opts, double* rho_out, double* e_out, md_workspace* ckpt,
                        md_stats* stats, cudaStream_t stream) {
     md_plan* pl = nullptr;
+    if (!stats) {   // asynchronous: launch, free the temporaries stream-ordered, report the launch
+        md_status st = plan_create(ham, poles, nodes, opts, rho_out, e_out, ckpt, true, stream, &pl, nullptr, true);
+        if (pl) plan_free(pl);
+        return st;
+    }
     md_status st = plan_create(ham, poles, nodes, opts, rho_out, e_out, ckpt, true, stream, &pl);
     if (st != MD_OK) return st;
     if (pl->n_sys == 0) {
@@ -1379,8 +1467,9 @@ extern "C" md_status md_lssgq_rules(const md_hamiltonian* ham, const md_nodes* n
             return set_error((_e == cudaErrorMemoryAllocation) ? MD_ERR_OOM : MD_ERR_CUDA,           \
                              std::string("CUDA: ") + cudaGetErrorString(_e) + " (" #expr ")");       \
     } while (0)
-    // every call ends synchronised with its stream, so the cached buffers
-    // are idle whenever a call grows them
+    // every call but an asynchronous md_density ends synchronised with its
+    // stream; wait for the last of those before using the scratch
+    LTRY(scratch_idle(H));
     const size_t need = P.slot_bytes * (size_t)grid;
     if (need > H.scratch_bytes) {
         LTRY(cudaStreamSynchronize(s));

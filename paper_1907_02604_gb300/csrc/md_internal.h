@@ -78,6 +78,17 @@ struct Ham {
     // cached work lists and per-node Lanczos results of md_lssgq_rules (grow-only)
     void* lz_buf = nullptr;
     size_t lz_bytes = 0;
+    // pinned staging of the uploads of asynchronous md_density calls, two in
+    // turn; an event marks when a buffer's last uploads have been read
+    struct Stage {
+        void* buf = nullptr;
+        size_t bytes = 0;
+        cudaEvent_t ev = nullptr;
+    } stage[2];
+    int stage_next = 0;
+    // recorded after each asynchronous md_density call: the scratch above is
+    // in use until it completes
+    cudaEvent_t scratch_ev = nullptr;
 };
 
 }  // namespace md
