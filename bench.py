@@ -183,13 +183,15 @@ def oracle_sample(w, timed, bar, target_s=20.0):
     error of the timed GPU densities and band energies against it on those
     nodes (max |d| / max |oracle| over the sample, and per node where
     rho_j > 1e-3 max rho).  `timed`: (node indices into the workload, GPU
-    rho, GPU e) per distinct timed batch; chunks of 1, 2, 4, ... 16 nodes are
-    taken from the batches in turn."""
+    rho, GPU e) per distinct timed batch; chunks of nodes doubling up to 16 are
+    taken from the batches in turn, starting at a quarter of the host threads
+    (so that every thread has systems to take from the first chunk on)."""
     from oracle import density as od
     H = od.build(w)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     t_used, solves, n_done = 0.0, 0, 0
     cursor = [0] * len(timed)
-    k, b = 1, 0
+    k, b = max(1, min(16, threads // 4)), 0
     g_rho, g_e, o_rho, o_e = [], [], [], []
     while t_used < target_s and any(c < len(t[0]) for c, t in zip(cursor, timed)):
         j = b % len(timed)
@@ -210,7 +212,6 @@ def oracle_sample(w, timed, bar, target_s=20.0):
         o_rho.append(res.rho)
         o_e.append(res.e_node)
         k = min(2 * k, 16)
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     cpu = {"value": solves / t_used, "unit": "solves/s", "cores": threads, "kind": "oracle",
            "sample": f"{n_done} nodes x {w.n_poles} poles of the timed batches of {w.name} "
                      f"(FP64 COCG, tol {w.tol:g}), {t_used:.1f} s"}
