@@ -543,7 +543,8 @@ __device__ __forceinline__ float2 nl_apply(const SolveParams& P, const Geo& G, c
 // kNl = false leaves out the nonlocal term (added elsewhere).
 template <class R, class C, int Q, class CIn, bool kNl = true>
 __device__ __forceinline__ C matvec_point(const SolveParams& P, const Geo& G, const Shared& S,
-                                          const CIn* __restrict__ v, int i, R zr, R zi, R diag) {
+                                          const CIn* __restrict__ v, int i, R zr, R zi, R diag,
+                                          uint2 rc_pre = make_uint2(0u, 0xFFFFFFFEu)) {
     const int c = (int)fdiv((uint32_t)i, G.div_plane);
     const int rem = i - c * G.plane;
     const int b = (int)fdiv((uint32_t)rem, G.div_row);
@@ -552,6 +553,11 @@ __device__ __forceinline__ C matvec_point(const SolveParams& P, const Geo& G, co
     const int gy = wrap_once(G.lo[1] + b, P.n[1]);
     const int gz = wrap_once(G.lo[2] + c, P.n[2]);
     const long long gi = gx + (long long)P.n[0] * (gy + (long long)P.n[1] * gz);
+    // the point's projector record first: its load (from the system's slot
+    // in device memory) then overlaps the stencil's
+    uint2 rc = make_uint2(0u, 0xFFFFFFFFu);
+    if (rc_pre.y != 0xFFFFFFFEu) rc = rc_pre;   // loaded ahead by the caller
+    else if (kNl && P.nonlocal && G.nl_rec) rc = G.nl_rec[i];
     const CIn vi = v[i];
     const R dg = diag + Tab<R>::V(P, gi) - zr;
     R yx = dg * re_of<R>(vi) + zi * im_of<R>(vi);
@@ -611,7 +617,6 @@ __device__ __forceinline__ C matvec_point(const SolveParams& P, const Geo& G, co
         }
     }
     if (kNl && P.nonlocal && G.nl_rec) {
-        const uint2 rc = G.nl_rec[i];
         if (rc.y != 0xFFFFFFFFu) {
 #pragma unroll
             for (int l = 0; l < 4; ++l) {

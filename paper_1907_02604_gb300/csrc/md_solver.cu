@@ -264,8 +264,15 @@ __global__ void __launch_bounds__(kMinB == 1 ? 1024 : 512, kMinB) k_cocg(const _
             if (P.nonlocal) nonlocal_coeffs<R, C>(P, G, S, p);
             {   // P2: Ap = (H_R - z) p ; p^T Ap
                 KSum<R> acc_re, acc_im;
+                // each point's projector record is loaded one point ahead
+                const bool pre = Mode::kMixed && P.nonlocal && G.nl_rec;
+                uint2 rc_next = make_uint2(0u, 0xFFFFFFFFu);
+                if (pre && threadIdx.x < G.n) rc_next = G.nl_rec[threadIdx.x];
                 for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
-                    const C y = matvec_point<R, C, Q, C>(P, G, S, p, i, zr, zi, diagR);
+                    const uint2 rc = rc_next;
+                    if (pre && i + (int)blockDim.x < G.n) rc_next = G.nl_rec[i + blockDim.x];
+                    const C y = matvec_point<R, C, Q, C>(P, G, S, p, i, zr, zi, diagR,
+                                                         pre ? rc : make_uint2(0u, 0xFFFFFFFEu));
                     Ap[i] = y;
                     const C pi = p[i];
                     acc_re.add(pi.x * y.x - pi.y * y.y);
