@@ -38,17 +38,17 @@ sys.path.insert(0, ROOT)
 METRIC = "(node,pole) solves/sec and density nodes/sec at rel err<=1e-6; matvec HBM GB/s"
 BYTES_PER_POINT_ITER = {"mixed": 80.0, "fp64": 160.0}
 # DRAM bytes (read + write) per region-point iteration of the solver kernel,
-# from one ncu capture (summary under profiles/: kernel k_cocg, bulk
-# workload, 32 nodes x 16 poles, 150-iteration cap), keyed by workload,
-# precision and launch shape (threads per CTA, CTAs per SM), scaled to a
-# full launch by its region-point iterations.  Valid only for the kernel
-# sources with the fingerprint below; any change to them makes the figure
-# stale (null).
-TRAFFIC_PER_POINT_ITER = {("bulk_mixed", "mixed", 512, 3): 124.3}
+# from one ncu capture of a full bench launch (summary under profiles/:
+# kernel k_cocg, bulk workload, one 256-node x 16-pole batch, 512 x 3),
+# keyed by workload, precision and launch shape (threads per CTA, CTAs per
+# SM), scaled to a launch by its region-point iterations.  Valid only for
+# the kernel sources with the fingerprint below; any change to them makes
+# the figure stale (null).
+TRAFFIC_PER_POINT_ITER = {("bulk_mixed", "mixed", 512, 3): 143.0}
 TRAFFIC_SOURCES = ("paper_1907_02604_gb300/csrc/md_solver.cu", "paper_1907_02604_gb300/csrc/md_solver.h",
                    "paper_1907_02604_gb300/csrc/md_device.cuh", "paper_1907_02604_gb300/csrc/md_internal.h",
                    "paper_1907_02604_gb300/csrc/md_operator.cuh")
-TRAFFIC_FINGERPRINT = "15df601444a11d3a:c156daa5b1c36f8f:6685de8068da134b:0fb5570fc87854c8:d8fb1f8a14608a26"
+TRAFFIC_FINGERPRINT = "00d7c0d826e328e7:0a35456717bedd0f:6685de8068da134b:6a946dc70a5a74c8:656548f983974f09"
 # FP64 operations (a multiply-add counted as two) per region point and COCG
 # iteration of the FP64 form at 8th order with projectors: stencil 12 offset
 # pairs x 6 = 72, diagonal 8, projector apply 24 and coefficients 12 (1.5

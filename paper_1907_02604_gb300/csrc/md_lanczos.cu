@@ -124,8 +124,15 @@ __global__ void __launch_bounds__(1024) k_lanczos(const __grid_constant__ SolveP
             if constexpr (kF32) {
                 const float scf = (float)sc, cbf = (float)cb;
                 KSum<float> acc;
+                // each point's projector record is loaded one point ahead
+                const bool pre = P.nonlocal && G.nl_rec;
+                uint2 rc_next = make_uint2(0u, 0xFFFFFFFFu);
+                if (pre && threadIdx.x < G.n) rc_next = G.nl_rec[threadIdx.x];
                 for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
-                    const float y = matvec_point<float, float, Q, float>(P, G, S, uc, i, 0.f, 0.f, (float)P.diag);
+                    const uint2 rc = rc_next;
+                    if (pre && i + (int)blockDim.x < G.n) rc_next = G.nl_rec[i + blockDim.x];
+                    const float y = matvec_point<float, float, Q, float>(P, G, S, uc, i, 0.f, 0.f, (float)P.diag,
+                                                                         pre ? rc : make_uint2(0u, 0xFFFFFFFEu));
                     const float wv = scf * y - cbf * up[i];
                     up[i] = wv;
                     acc.add(uc[i] * wv);
