@@ -243,8 +243,10 @@ __global__ void __launch_bounds__(kMinB == 1 ? 1024 : 512, kMinB) k_cocg(const _
                     const float4* r4 = reinterpret_cast<const float4*>(r);
                     float4* p4 = reinterpret_cast<float4*>(p);
                     const int npair = G.n >> 1;
+                    const uint64_t pol = l2_evict_first_policy();
                     for (int k = threadIdx.x; k < npair; k += blockDim.x) {
-                        const float4 a = r4[k], b = p4[k];
+                        const float4 a = ld_stream(r4 + k, pol), b = ld_stream(p4 + k, pol);
+                        // the new direction keeps the default priority: the next two passes re-read it
                         p4[k] = make_float4(a.x + br * b.x - bi * b.y, a.y + br * b.y + bi * b.x,
                                             a.z + br * b.z - bi * b.w, a.w + br * b.w + bi * b.z);
                     }
@@ -266,14 +268,16 @@ __global__ void __launch_bounds__(kMinB == 1 ? 1024 : 512, kMinB) k_cocg(const _
                 KSum<R> acc_re, acc_im;
                 // each point's projector record is loaded one point ahead
                 const bool pre = Mode::kMixed && P.nonlocal && G.nl_rec;
+                const uint64_t pol = l2_evict_first_policy();
                 uint2 rc_next = make_uint2(0u, 0xFFFFFFFFu);
-                if (pre && threadIdx.x < G.n) rc_next = G.nl_rec[threadIdx.x];
+                if (pre && threadIdx.x < G.n) rc_next = ld_stream(G.nl_rec + threadIdx.x, pol);
                 for (int i = threadIdx.x; i < G.n; i += blockDim.x) {
                     const uint2 rc = rc_next;
-                    if (pre && i + (int)blockDim.x < G.n) rc_next = G.nl_rec[i + blockDim.x];
+                    if (pre && i + (int)blockDim.x < G.n) rc_next = ld_stream(G.nl_rec + i + blockDim.x, pol);
                     const C y = matvec_point<R, C, Q, C>(P, G, S, p, i, zr, zi, diagR,
                                                          pre ? rc : make_uint2(0u, 0xFFFFFFFEu));
-                    Ap[i] = y;
+                    if constexpr (Mode::kMixed) st_stream(reinterpret_cast<float2*>(Ap + i), y, pol);
+                    else Ap[i] = y;
                     const C pi = p[i];
                     acc_re.add(pi.x * y.x - pi.y * y.y);
                     acc_im.add(pi.x * y.y + pi.y * y.x);
@@ -312,9 +316,10 @@ __global__ void __launch_bounds__(kMinB == 1 ? 1024 : 512, kMinB) k_cocg(const _
                     float4* d4 = reinterpret_cast<float4*>(dx);
                     float4* r4 = reinterpret_cast<float4*>(r);
                     const int npair = G.n >> 1;
+                    const uint64_t pol = l2_evict_first_policy();
                     for (int k = threadIdx.x; k < npair; k += blockDim.x) {
-                        const float4 pv = p4[k], qv = q4[k];
-                        float4 d = d4[k], rv = r4[k];
+                        const float4 pv = ld_stream(p4 + k, pol), qv = ld_stream(q4 + k, pol);
+                        float4 d = ld_stream(d4 + k, pol), rv = ld_stream(r4 + k, pol);
                         d.x += ar * pv.x - ai * pv.y;
                         d.y += ar * pv.y + ai * pv.x;
                         d.z += ar * pv.z - ai * pv.w;
@@ -323,8 +328,8 @@ __global__ void __launch_bounds__(kMinB == 1 ? 1024 : 512, kMinB) k_cocg(const _
                         rv.y -= ar * qv.y + ai * qv.x;
                         rv.z -= ar * qv.z - ai * qv.w;
                         rv.w -= ar * qv.w + ai * qv.z;
-                        d4[k] = d;
-                        r4[k] = rv;
+                        st_stream(d4 + k, d, pol);
+                        st_stream(r4 + k, rv, pol);
                         if (P.multishift && (G.src >> 1) == k)
                             S.rj = (G.src & 1) ? make_double2(rv.z, rv.w) : make_double2(rv.x, rv.y);
                         s_re.add(rv.x * rv.x - rv.y * rv.y + (rv.z * rv.z - rv.w * rv.w));
