@@ -185,7 +185,8 @@ md_status md_hamiltonian_destroy(md_hamiltonian* ham);
 /* Copies V (N doubles) to device memory V_out, stream-ordered. */
 md_status md_hamiltonian_potential(const md_hamiltonian* ham, double* V_out, void* stream);
 
-/* Replaces V by the device array V_in (N doubles), stream-ordered; used to
+/* Replaces V by the device array V_in (N doubles), stream-ordered (and
+ * ordered after the last asynchronous md_density on the handle); used to
  * differentiate with respect to the local potential directly. */
 md_status md_hamiltonian_set_potential(md_hamiltonian* ham, const double* V_in, void* stream);
 

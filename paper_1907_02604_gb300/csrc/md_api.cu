@@ -99,23 +99,28 @@ md_status check_device() {
 }
 
 void free_ham(Ham& H) {
+    // an asynchronous md_density may still be reading the operator, the
+    // scratch or a staging buffer: wait for it first
+    if (H.scratch_ev) {
+        cudaEventSynchronize(H.scratch_ev);
+        cudaEventDestroy(H.scratch_ev);
+        H.scratch_ev = nullptr;
+    }
+    for (Ham::Stage& sg : H.stage) {
+        if (sg.ev) {
+            cudaEventSynchronize(sg.ev);
+            cudaEventDestroy(sg.ev);
+            sg.ev = nullptr;
+        }
+        if (sg.buf) cudaFreeHost(sg.buf);
+        sg.buf = nullptr;
+    }
     void* ptrs[] = {H.V, H.V32, H.atom_xyz, H.atom_depth, H.atom_sigma, H.proj_i0, H.proj_len,
                     H.proj_d, H.proj_g, H.proj_d32, H.proj_g32, H.proj_C, H.proj_absum,
                     H.proj_C32, H.proj_rows, H.pl_ptr, H.pl_atom, H.pl_val32, H.pl_val64,
                     H.scratch, H.lz_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    for (Ham::Stage& sg : H.stage) {
-        if (sg.ev) {
-            cudaEventSynchronize(sg.ev);
-            cudaEventDestroy(sg.ev);
-        }
-        if (sg.buf) cudaFreeHost(sg.buf);
-    }
-    if (H.scratch_ev) {
-        cudaEventSynchronize(H.scratch_ev);
-        cudaEventDestroy(H.scratch_ev);
-    }
 }
 
 // Host wait until the last asynchronous md_density call on the handle has
@@ -2051,6 +2056,11 @@ md_status md_plan_destroy(md_plan* plan) {
 md_status md_hamiltonian_set_potential(md_hamiltonian* ham, const double* V_in, void* stream) {
     clear_error();
     if (!ham || !V_in) return set_error(MD_ERR_INVALID, "ham and V_in are required");
+    // after any asynchronous md_density still reading the old potential
+    if (ham->h.scratch_ev) {
+        const cudaError_t e = cudaStreamWaitEvent((cudaStream_t)stream, ham->h.scratch_ev, 0);
+        if (e != cudaSuccess) return set_error(MD_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    }
     return set_potential_device(ham->h, V_in, stream);
 }
 

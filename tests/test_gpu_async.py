@@ -91,3 +91,28 @@ def test_async_empty_and_invalid():
     with pytest.raises(MacroDFTError):
         density(ham, z, wt, w.nodes[:2], np.array([-1, 2], np.int32), SolverOptions(), sync=False)
     torch.cuda.synchronize()
+
+
+def test_set_potential_waits_for_pending_async():
+    """A new potential set on another stream does not reach a pending
+    asynchronous solve: md_hamiltonian_set_potential is ordered after it."""
+    import torch
+    from paper_1907_02604_gb300 import SolverOptions, density
+    w, ham, z, wt = _setup()
+    opts = SolverOptions(tol=w.tol)
+    ref, _, _ = density(ham, z, wt, w.nodes, w.halfwidth, opts)
+    V0 = ham.potential()
+    V1 = V0 + 0.5
+    a, b = torch.cuda.Stream(), torch.cuda.Stream()
+    a.wait_stream(torch.cuda.current_stream())
+    b.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(a):
+        rho_a = density(ham, z, wt, w.nodes, w.halfwidth, opts, stream=a, sync=False)[0]
+    with torch.cuda.stream(b):
+        ham.set_potential(V1, stream=b)
+    a.synchronize()
+    b.synchronize()
+    assert rel_err(rho_a.cpu().numpy(), ref.cpu().numpy()) <= 1e-12
+    assert torch.equal(ham.potential(), V1)
+    ham.set_potential(V0)
+    torch.cuda.synchronize()
