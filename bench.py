@@ -226,6 +226,15 @@ def oracle_sample(w, timed, bar, target_s=20.0):
     return cpu, parity
 
 
+def workload_config(w, bs, prec):
+    """The workload part of the line's config, shared by both arms."""
+    lo, hi = int(w.halfwidth.min()), int(w.halfwidth.max())
+    region = f"{2 * lo + 1}^3" if lo == hi else f"{2 * lo + 1}^3..{2 * hi + 1}^3"
+    return {"workload": w.name, "nodes_per_step": bs, "poles": w.n_poles, "region": region,
+            "grid": list(w.shape), "atoms": len(w.atoms), "fd_order": w.fd_order, "precision": prec,
+            "tol": w.tol}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -260,8 +269,7 @@ def run_reference(args, world, rank):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w.name, "nodes_per_step": per_step_nodes, "poles": w.n_poles,
-                      "threads": threads},
+           "config": workload_config(w, min(args.nodes_per_step, len(w.nodes)), args.precision or w.precision),
            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": threads, "kind": "oracle",
                             "sample": f"{per_step_nodes} nodes x {w.n_poles} poles per step of {w.name} "
                                       f"({per_step_nodes * w.n_poles} systems over {threads} threads)"},
@@ -731,10 +739,7 @@ def main():
         "vs_baseline": None,
         "dtype": "f32+f64" if prec == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "nodes_per_step": bs, "poles": w.n_poles,
-                   "region": (f"{2 * int(w.halfwidth.min()) + 1}^3" if w.halfwidth.min() == w.halfwidth.max() else
-                              f"{2 * int(w.halfwidth.min()) + 1}^3..{2 * int(w.halfwidth.max()) + 1}^3"), "grid": list(w.shape), "atoms": len(w.atoms),
-                   "fd_order": w.fd_order, "precision": prec, "tol": w.tol,
+        "config": {**workload_config(w, bs, prec),
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB written)",
                    "pole_expansion": expansion,
                    "parallelism": (f"nodes sharded over {world} GPU(s), no collective in the timed region"
