@@ -23,3 +23,17 @@ def test_reference_arm_json_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_config_is_the_workload_config():
+    """Both arms print the same workload description (bench.workload_config)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from synthetic import make_workload
+    w = make_workload("small_fp64")
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                          "--workload", "small_fp64"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads([ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1])
+    assert d["config"] == bench.workload_config(w, min(256, len(w.nodes)), w.precision)
+    assert d["config"]["region"] == "21^3" and d["config"]["grid"] == list(w.shape)
