@@ -116,3 +116,43 @@ def test_set_potential_waits_for_pending_async():
     assert torch.equal(ham.potential(), V1)
     ham.set_potential(V0)
     torch.cuda.synchronize()
+
+
+def test_async_checkpoint_feeds_the_adjoint():
+    """The checkpoint written by an asynchronous solve gives the same dL/dV
+    as the one written by a synchronising solve."""
+    import torch
+    from paper_1907_02604_gb300 import SolverOptions, Workspace, density, density_adjoint
+    w, ham, z, wt = _setup(n=6)
+    opts = SolverOptions(tol=w.tol)
+    ones = torch.ones(len(w.nodes), dtype=torch.float64, device="cuda")
+    ws_s = Workspace(ham, w.nodes, w.halfwidth, w.n_poles)
+    density(ham, z, wt, w.nodes, w.halfwidth, opts, checkpoint=ws_s)
+    g_s = density_adjoint(ham, z, wt, w.nodes, w.halfwidth, ones, None, opts, checkpoint=ws_s)[0]
+    ws_a = Workspace(ham, w.nodes, w.halfwidth, w.n_poles)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        density(ham, z, wt, w.nodes, w.halfwidth, opts, checkpoint=ws_a, stream=s, sync=False)
+    s.synchronize()
+    g_a = density_adjoint(ham, z, wt, w.nodes, w.halfwidth, ones, None, opts, checkpoint=ws_a)[0]
+    assert torch.equal(g_a, g_s)
+
+
+@pytest.mark.parametrize("kernel,method", [("cluster", "cocg"), ("auto", "shifted")])
+def test_async_other_kernels(kernel, method):
+    """The asynchronous form on the cluster kernel and with shifted COCG.
+    The cluster kernel sums its projector partials with shared-memory
+    atomics, so two of its runs agree to rounding, not bit for bit."""
+    import torch
+    from paper_1907_02604_gb300 import SolverOptions, density
+    w, ham, z, wt = _setup("bulk_mixed", 4)
+    opts = SolverOptions(tol=w.tol, precision="mixed", kernel=kernel, method=method)
+    ref, _, st = density(ham, z, wt, w.nodes, w.halfwidth, opts)
+    assert st["n_converged"] == w.n_systems
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        rho = density(ham, z, wt, w.nodes, w.halfwidth, opts, stream=s, sync=False)[0]
+    s.synchronize()
+    assert rel_err(rho.cpu().numpy(), ref.cpu().numpy()) <= (1e-10 if kernel == "cluster" else 1e-12)
